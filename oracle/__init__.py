@@ -1,0 +1,295 @@
+"""FP64 CPU oracle for the single-pulse search (Adamek & Armour, arXiv:1611.09704).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the product library
+never does, and it shares no code with the CUDA path.
+
+The arithmetic lives in ``spd_oracle.c`` (plain C, FP64), built into
+``oracle/_build/liboracle.so`` by :func:`build`.  This module only marshals
+numpy arrays.  Function by function:
+
+- :func:`twopass`, :func:`chan_stream`, :func:`chan_merge` -- Sec. 2.1: the
+  two-pass definition of mean and population sd, Eq. 1 and Eq. 2.
+- :func:`plane_msd`, :func:`plane_msd_chan` -- the MSD of a DM x time plane
+  (whole plane or per row), by definition and by the block scheme of Sec. 2.1.
+- :func:`plane_sd_nmax`, :func:`sigma_table` -- Sec. 2.2, Eq. 4 and Eq. 5.
+- :func:`boxcar_sums`, :func:`boxcar_snr` -- Sec. 2.3 and Algorithm 1.
+- :func:`threshold` -- Sec. 2.4.
+- :func:`search` -- the four steps in order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+SIGMA_SQRTN, SIGMA_LINEAR, SIGMA_LINEAR_EXCESS = 0, 1, 2
+SCOPE_GLOBAL, SCOPE_PER_ROW = 0, 1
+_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over rows, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+            "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.oracle_twopass.argtypes = [P, I64, P, P]
+    lib.oracle_chan_stream.argtypes = [P, I64, P, P]
+    lib.oracle_chan_merge.argtypes = [D, D, D, D, D, D, P, P]
+    lib.oracle_plane_msd.argtypes = [P, I32, I64, I64, I64, P, P, I32, P, P]
+    lib.oracle_plane_msd.restype = I32
+    lib.oracle_plane_msd_chan.argtypes = [P, I32, I64, I64, I64, P, P, I64, I32, P, P]
+    lib.oracle_plane_msd_chan.restype = I32
+    lib.oracle_plane_sd_nmax.argtypes = [P, I32, I64, I64, I64, P, P, I32, I32, P]
+    lib.oracle_plane_sd_nmax.restype = I32
+    lib.oracle_sigma_table.argtypes = [I32, D, D, I32, P, I32, P]
+    lib.oracle_sigma_table.restype = I32
+    lib.oracle_boxcar_sums.argtypes = [P, I32, I64, I64, I64, P, P, I32, P]
+    lib.oracle_boxcar_sums.restype = I32
+    lib.oracle_boxcar_snr.argtypes = [P, I32, I64, I64, I64, P, P, I32, P, P, P, P,
+                                      I32, I64, I64, P, P]
+    lib.oracle_boxcar_snr.restype = I32
+    lib.oracle_threshold.argtypes = [P, P, I64, I64, I64, D, P, P, P, P, I64]
+    lib.oracle_threshold.restype = I64
+    lib.oracle_dequant_row.argtypes = [P, I32, I64, P, P, I64, I64, P]
+    lib.oracle_num_threads.restype = I32
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's row loops use."""
+    return int(_load().oracle_num_threads())
+
+
+@dataclass
+class Plane:
+    """A DM x time plane on the host: ``data`` is float32 [n_dm, stride] or the
+    uint16 bit patterns of FP16 / BF16; ``n_samp`` <= stride valid samples per
+    row; optional float32 per-row ``scale`` / ``offset``
+    (value = fmaf(scale, q, offset))."""
+    data: np.ndarray
+    dtype: str = "f32"
+    n_samp: int | None = None
+    scale: np.ndarray | None = None
+    offset: np.ndarray | None = None
+
+    def __post_init__(self):
+        if self.dtype not in _DTYPES:
+            raise ValueError(f"dtype {self.dtype!r}")
+        want = np.float32 if self.dtype == "f32" else np.uint16
+        self.data = np.ascontiguousarray(self.data, dtype=want)
+        if self.data.ndim != 2:
+            raise ValueError("plane must be 2-D")
+        if self.n_samp is None:
+            self.n_samp = self.data.shape[1]
+        if self.scale is not None:
+            self.scale = np.ascontiguousarray(self.scale, dtype=np.float32)
+        if self.offset is not None:
+            self.offset = np.ascontiguousarray(self.offset, dtype=np.float32)
+
+    @property
+    def n_dm(self) -> int:
+        return self.data.shape[0]
+
+    @property
+    def stride(self) -> int:
+        return self.data.shape[1]
+
+    def args(self):
+        return (_ptr(self.data), _DTYPES[self.dtype], self.n_dm, self.n_samp,
+                self.stride, _ptr(self.scale), _ptr(self.offset))
+
+    def values(self) -> np.ndarray:
+        """Dequantised float64 values [n_dm, n_samp] (small planes only)."""
+        out = np.empty((self.n_dm, self.n_samp), dtype=np.float64)
+        lib = _load()
+        for r in range(self.n_dm):
+            lib.oracle_dequant_row(_ptr(self.data), _DTYPES[self.dtype], self.stride,
+                                   _ptr(self.scale), _ptr(self.offset), r, self.n_samp,
+                                   out[r].ctypes.data)
+        return out
+
+
+def as_plane(x, **kw) -> Plane:
+    return x if isinstance(x, Plane) else Plane(np.asarray(x), **kw)
+
+
+# ----------------------------------------------------------------- Sec. 2.1
+
+def twopass(x) -> tuple[float, float]:
+    """Definition: (mean, population sd) of a 1-D sample."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    m, s = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_twopass(_ptr(x), x.size, ctypes.byref(m), ctypes.byref(s))
+    return m.value, s.value
+
+
+def chan_stream(x) -> tuple[float, float]:
+    """Eq. 1 over a 1-D sample: returns (T, S)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    T, S = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_chan_stream(_ptr(x), x.size, ctypes.byref(T), ctypes.byref(S))
+    return T.value, S.value
+
+
+def chan_merge(m, Ta, Sa, n, Tb, Sb) -> tuple[float, float]:
+    """Eq. 2: (T, S) of the union of an m-sample set and an n-sample set."""
+    T, S = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_chan_merge(float(m), float(Ta), float(Sa), float(n), float(Tb),
+                              float(Sb), ctypes.byref(T), ctypes.byref(S))
+    return T.value, S.value
+
+
+def plane_msd(plane, scope: int = SCOPE_GLOBAL):
+    """Two-pass MSD of a plane: arrays (mean, sd) of length 1 or n_dm."""
+    p = as_plane(plane)
+    k = 1 if scope == SCOPE_GLOBAL else p.n_dm
+    mean, sd = np.zeros(k), np.zeros(k)
+    rc = _load().oracle_plane_msd(*p.args(), scope, _ptr(mean), _ptr(sd))
+    if rc:
+        raise ValueError(f"oracle_plane_msd rc={rc}")
+    return mean, sd
+
+
+def plane_msd_chan(plane, block: int, scope: int = SCOPE_GLOBAL):
+    """Block scheme of Sec. 2.1 (Eq. 1 per block, Eq. 2 merges)."""
+    p = as_plane(plane)
+    k = 1 if scope == SCOPE_GLOBAL else p.n_dm
+    mean, sd = np.zeros(k), np.zeros(k)
+    rc = _load().oracle_plane_msd_chan(*p.args(), int(block), scope, _ptr(mean), _ptr(sd))
+    if rc:
+        raise ValueError(f"oracle_plane_msd_chan rc={rc}")
+    return mean, sd
+
+
+# ----------------------------------------------------------------- Sec. 2.2
+
+def plane_sd_nmax(plane, nmax: int, scope: int = SCOPE_GLOBAL) -> np.ndarray:
+    """sigma_Nmax of Eq. 5: measured sd of the Nmax-sample boxcar series."""
+    p = as_plane(plane)
+    k = 1 if scope == SCOPE_GLOBAL else p.n_dm
+    out = np.zeros(k)
+    rc = _load().oracle_plane_sd_nmax(*p.args(), int(nmax), scope, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle_plane_sd_nmax rc={rc}")
+    return out
+
+
+def sigma_table(mode: int, sd: float, widths, sd_nmax: float = 0.0, nmax: int = 0):
+    """sigma_N per width: Eq. 4 (mode 0) or Eq. 5 (modes 1, 2)."""
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    out = np.zeros(w.size)
+    rc = _load().oracle_sigma_table(int(mode), float(sd), float(sd_nmax), int(nmax),
+                                    _ptr(w), w.size, _ptr(out))
+    if rc:
+        raise ValueError("sigma_table: Eq. 5 needs nmax >= 2")
+    return out
+
+
+# ----------------------------------------------------------------- Sec. 2.3
+
+def boxcar_sums(plane, w: int) -> np.ndarray:
+    """B_w(i) for every start i (NaN where the window passes the row end)."""
+    p = as_plane(plane)
+    out = np.empty((p.n_dm, p.n_samp))
+    _load().oracle_boxcar_sums(*p.args(), int(w), _ptr(out))
+    return out
+
+
+def boxcar_snr(plane, mean, sd, sigma_tab, widths, scope: int = SCOPE_GLOBAL,
+               rows: tuple[int, int] | None = None):
+    """Algorithm 1: per-sample (highest SNR, winning width) for rows [r0, r1).
+
+    mean, sd: arrays of length 1 (global scope) or n_dm (per row);
+    sigma_tab: [entries, n_widths] sigma_w."""
+    p = as_plane(plane)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    r0, r1 = rows if rows is not None else (0, p.n_dm)
+    mean = np.ascontiguousarray(np.atleast_1d(mean), dtype=np.float64)
+    sd = np.ascontiguousarray(np.atleast_1d(sd), dtype=np.float64)
+    tab = np.ascontiguousarray(np.atleast_2d(sigma_tab), dtype=np.float64)
+    best = np.empty((r1 - r0, p.n_samp))
+    win = np.empty((r1 - r0, p.n_samp), dtype=np.int32)
+    rc = _load().oracle_boxcar_snr(*p.args(), scope, _ptr(mean), _ptr(sd), _ptr(tab),
+                                   _ptr(w), w.size, r0, r1, _ptr(best), _ptr(win))
+    if rc:
+        raise ValueError(f"oracle_boxcar_snr rc={rc}")
+    return best, win
+
+
+# ----------------------------------------------------------------- Sec. 2.4
+
+def threshold(best, width, thr: float, row0: int = 0):
+    """Candidates with best >= thr, in (dm, sample) order, as a structured array."""
+    best = np.ascontiguousarray(best, dtype=np.float64)
+    width = np.ascontiguousarray(width, dtype=np.int32)
+    n_rows, n_samp = best.shape
+    lib = _load()
+    cnt = lib.oracle_threshold(_ptr(best), _ptr(width), n_rows, n_samp, row0, float(thr),
+                               None, None, None, None, 0)
+    dm = np.empty(cnt, np.int32)
+    sm = np.empty(cnt, np.int32)
+    snr = np.empty(cnt, np.float64)
+    wd = np.empty(cnt, np.int32)
+    lib.oracle_threshold(_ptr(best), _ptr(width), n_rows, n_samp, row0, float(thr),
+                         _ptr(dm), _ptr(sm), _ptr(snr), _ptr(wd), cnt)
+    out = np.empty(cnt, dtype=[("dm", np.int32), ("sample", np.int32),
+                               ("snr", np.float64), ("width", np.int32)])
+    out["dm"], out["sample"], out["snr"], out["width"] = dm, sm, snr, wd
+    return out
+
+
+# ------------------------------------------------------------ whole path
+
+def msd_and_sigma(plane, widths, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=0):
+    """Steps (a) and the sigma_w of (c): (mean, sd, sd_nmax, sigma_tab)."""
+    p = as_plane(plane)
+    mean, sd = plane_msd(p, scope)
+    widths = np.asarray(widths, dtype=np.int32)
+    if sigma_mode != SIGMA_SQRTN:
+        nmax = int(nmax or widths[-1])
+        sdn = plane_sd_nmax(p, nmax, scope)
+    else:
+        sdn = np.zeros_like(sd)
+    tab = np.stack([sigma_table(sigma_mode, sd[e], widths, sdn[e], nmax)
+                    for e in range(sd.size)])
+    return mean, sd, sdn, tab
+
+
+def search(plane, widths, thr, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=0,
+           rows=None):
+    """The four steps in the paper's order; returns (candidates, best, width, msd)."""
+    p = as_plane(plane)
+    mean, sd, sdn, tab = msd_and_sigma(p, widths, sigma_mode, scope, nmax)
+    best, win = boxcar_snr(p, mean, sd, tab, widths, scope, rows)
+    r0 = rows[0] if rows else 0
+    cands = threshold(best, win, thr, row0=r0)
+    return cands, best, win, (mean, sd, sdn, tab)

@@ -1,0 +1,354 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a closed form,
+a hand-evaluated table (tests/golden/), an invariant, a library routine, or a
+brute-force enumeration written independently of the oracle's loops.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rows(name):
+    out = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                out.append(line.split())
+    return out
+
+
+# ------------------------------------------------------------ Sec. 2.1, Eq. 1/2
+
+def test_chan_stream_hand_values():
+    """Eq. 1 with the square restored reproduces hand-evaluated (T, S)."""
+    for xs, T, S in _rows("chan_small.txt"):
+        x = np.array([float(v) for v in xs.split(",")])
+        t, s = oracle.chan_stream(x)
+        assert t == pytest.approx(float(T), rel=0, abs=1e-12)
+        assert s == pytest.approx(float(S), rel=1e-14, abs=1e-12)
+
+
+def test_chan_first_step_closed_form():
+    """j = 2: S must be (x2 - x1)^2 / 2, the population S of two samples."""
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        a, b = rng.normal(size=2) * 10
+        _, s = oracle.chan_stream([a, b])
+        assert s == pytest.approx((b - a) ** 2 / 2, rel=1e-13, abs=1e-13)
+
+
+def test_eq1_as_printed_is_not_the_variance():
+    """The printed update (no square) disagrees with the definition, which is
+    why the oracle reads Eq. 1 with the square (planted on the CPU)."""
+    x = np.array([1.0, 2.0, 4.0])
+    t, s = 0.0, 0.0
+    for j, xj in enumerate(x, start=1):
+        t += xj
+        if j > 1:
+            s += (j * xj - t) / (j * (j - 1))
+    assert abs(s - 42 / 9) > 1.0
+    _, s_ok = oracle.chan_stream(x)
+    assert s_ok == pytest.approx(42 / 9, rel=1e-14)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 1000, 4097])
+def test_chan_stream_equals_twopass(n):
+    rng = np.random.default_rng(n)
+    x = rng.normal(100.0, 12.0, size=n)
+    t, s = oracle.chan_stream(x)
+    mu, sd = oracle.twopass(x)
+    assert t / n == pytest.approx(np.mean(x), rel=1e-13)
+    assert mu == pytest.approx(np.mean(x), rel=1e-13)
+    assert math.sqrt(s / n) == pytest.approx(np.std(x), rel=1e-11, abs=1e-12)
+    assert sd == pytest.approx(np.std(x), rel=1e-12, abs=1e-13)
+
+
+def test_chan_merge_any_split_and_tree():
+    """Eq. 2: every split point and a random merge tree give the stream result."""
+    rng = np.random.default_rng(11)
+    x = rng.normal(-3.0, 2.5, size=257)
+    T0, S0 = oracle.chan_stream(x)
+    for cut in [1, 2, 100, 128, 256]:
+        Ta, Sa = oracle.chan_stream(x[:cut])
+        Tb, Sb = oracle.chan_stream(x[cut:])
+        T, S = oracle.chan_merge(cut, Ta, Sa, x.size - cut, Tb, Sb)
+        assert T == pytest.approx(T0, rel=1e-13, abs=1e-12)
+        assert S == pytest.approx(S0, rel=1e-12)
+    # random binary tree over random-size pieces
+    cuts = np.sort(rng.choice(np.arange(1, x.size), size=20, replace=False))
+    parts = [(p.size, *oracle.chan_stream(p)) for p in np.split(x, cuts)]
+    while len(parts) > 1:
+        k = int(rng.integers(0, len(parts) - 1))
+        (m, Ta, Sa), (n, Tb, Sb) = parts[k], parts[k + 1]
+        parts[k: k + 2] = [(m + n, *oracle.chan_merge(m, Ta, Sa, n, Tb, Sb))]
+    n, T, S = parts[0]
+    assert n == x.size
+    assert T == pytest.approx(T0, rel=1e-13, abs=1e-12)
+    assert S == pytest.approx(np.var(x) * x.size, rel=1e-12)
+
+
+def test_chan_merge_empty_side():
+    assert oracle.chan_merge(0, 0, 0, 3, 6.0, 2.0) == (6.0, 2.0)
+    assert oracle.chan_merge(3, 6.0, 2.0, 0, 0, 0) == (6.0, 2.0)
+
+
+def test_plane_msd_ramp_closed_form():
+    """x = a + b i: mean a + b (n-1)/2, variance b^2 (n^2 - 1)/12."""
+    n_dm, n = 3, 5000
+    a, b = 7.0, 0.25
+    row = a + b * np.arange(n)
+    plane = np.tile(row, (n_dm, 1)).astype(np.float32)
+    for fn in (lambda p: oracle.plane_msd(p, oracle.SCOPE_PER_ROW),
+               lambda p: oracle.plane_msd_chan(p, 777, oracle.SCOPE_PER_ROW)):
+        mean, sd = fn(plane)
+        assert np.allclose(mean, a + b * (n - 1) / 2, rtol=1e-13)
+        assert np.allclose(sd, math.sqrt(b * b * (n * n - 1) / 12), rtol=1e-12)
+
+
+def test_plane_msd_constant_is_zero_sd():
+    plane = np.full((4, 999), 3.5, dtype=np.float32)
+    mean, sd = oracle.plane_msd(plane)
+    assert mean[0] == 3.5 and sd[0] == 0.0
+    mean, sd = oracle.plane_msd_chan(plane, 64)
+    assert mean[0] == 3.5 and sd[0] == 0.0
+
+
+@pytest.mark.parametrize("block", [1, 7, 256, 10 ** 6])
+def test_plane_block_scheme_equals_definition(block):
+    """The two-kernel block scheme of Sec. 2.1 equals numpy's mean / std."""
+    rng = np.random.default_rng(block)
+    plane = rng.normal(100.0, 12.0, size=(6, 3001)).astype(np.float32)
+    ref = plane.astype(np.float64)
+    for scope in (oracle.SCOPE_GLOBAL, oracle.SCOPE_PER_ROW):
+        m1, s1 = oracle.plane_msd(plane, scope)
+        m2, s2 = oracle.plane_msd_chan(plane, block, scope)
+        if scope == oracle.SCOPE_GLOBAL:
+            mr, sr = np.array([ref.mean()]), np.array([ref.std()])
+        else:
+            mr, sr = ref.mean(axis=1), ref.std(axis=1)
+        assert np.allclose(m1, mr, rtol=1e-13) and np.allclose(m2, mr, rtol=1e-12)
+        assert np.allclose(s1, sr, rtol=1e-12) and np.allclose(s2, sr, rtol=1e-10)
+
+
+def test_ragged_stride_is_ignored():
+    """Samples past n_samp (here NaN) never enter any oracle result."""
+    rng = np.random.default_rng(3)
+    full = rng.normal(size=(3, 130)).astype(np.float32)
+    padded = np.full((3, 160), np.nan, dtype=np.float32)
+    padded[:, :130] = full
+    p = oracle.Plane(padded, n_samp=130)
+    m, s = oracle.plane_msd(p)
+    assert m[0] == pytest.approx(full.astype(np.float64).mean(), rel=1e-13)
+    assert s[0] == pytest.approx(full.astype(np.float64).std(), rel=1e-12)
+    b = oracle.boxcar_sums(p, 5)
+    assert np.isfinite(b[:, :126]).all() and np.isnan(b[:, 126:]).all()
+
+
+# --------------------------------------------------------- dequantisation
+
+def test_half_and_bf16_decoding_match_library_conversions():
+    import torch
+    bits = np.arange(0, 65536, dtype=np.uint32).astype(np.uint16)
+    bits = bits[(bits & 0x7C00) != 0x7C00]  # drop inf / nan patterns
+    plane = bits.reshape(1, -1)
+    got = oracle.Plane(plane, dtype="f16").values()[0]
+    want = bits.view(np.float16).astype(np.float64)
+    assert np.array_equal(got, want)
+    b2 = np.arange(0, 65536, dtype=np.uint32).astype(np.uint16)
+    b2 = b2[(b2 & 0x7F80) != 0x7F80]
+    got = oracle.Plane(b2.reshape(1, -1), dtype="bf16").values()[0]
+    want = torch.from_numpy(b2.view(np.int16)).view(torch.bfloat16).double().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_scale_offset_is_fp32_fma():
+    q = np.array([[1.0, 2.0, 3.0]], dtype=np.float16)
+    sc = np.array([0.1], np.float32)
+    off = np.array([5.0], np.float32)
+    got = oracle.Plane(q.view(np.uint16), dtype="f16", scale=sc, offset=off).values()[0]
+    # an FP32 fused multiply-add rounds once: emulate with float64 then round
+    want = (np.float64(sc[0]) * q.astype(np.float64)[0] + np.float64(off[0])).astype(np.float32)
+    assert np.array_equal(got, want.astype(np.float64))
+
+
+# ------------------------------------------------------------ Sec. 2.2, Eq. 4/5
+
+def test_sigma_table_hand_values():
+    rows = _rows("eq5_sigma_table.txt")
+    widths = [int(r[0]) for r in rows]
+    cols = np.array([[float(v) for v in r[1:]] for r in rows])
+    assert np.allclose(oracle.sigma_table(oracle.SIGMA_SQRTN, 1.0, widths), cols[:, 0],
+                       rtol=1e-15)
+    assert np.allclose(oracle.sigma_table(oracle.SIGMA_LINEAR, 1.0, widths, 10.0, 4),
+                       cols[:, 1], rtol=1e-15)
+    assert np.allclose(oracle.sigma_table(oracle.SIGMA_LINEAR_EXCESS, 1.0, widths, 10.0, 4),
+                       cols[:, 2], rtol=1e-15)
+
+
+def test_eq5_endpoints():
+    """E reading: exact at N = 1 and N = Nmax.  L as printed: sigma at N = 1 and
+    sigma_Nmax + sqrt(Nmax) sigma at N = Nmax."""
+    sd, sdn, nmax = 1.7, 30.0, 256
+    e = oracle.sigma_table(oracle.SIGMA_LINEAR_EXCESS, sd, [1, nmax], sdn, nmax)
+    l_ = oracle.sigma_table(oracle.SIGMA_LINEAR, sd, [1, nmax], sdn, nmax)
+    assert e[0] == pytest.approx(sd) and e[1] == pytest.approx(sdn)
+    assert l_[0] == pytest.approx(sd) and l_[1] == pytest.approx(sdn + 16 * sd)
+
+
+def test_sqrtN_on_gaussian_noise():
+    """Eq. 3/4: the empirical sd of B_N on N(0, sd^2) noise is sqrt(N) sd within
+    3 standard errors (about n/N independent windows)."""
+    rng = np.random.default_rng(42)
+    sd = 2.0
+    plane = rng.normal(0.0, sd, size=(4, 50000)).astype(np.float32)
+    for N in (1, 4, 16, 64):
+        b = oracle.boxcar_sums(plane, N)
+        emp = np.nanstd(b)
+        n_eff = plane.size / N
+        se = sd * math.sqrt(N) / math.sqrt(2 * n_eff)
+        assert abs(emp - sd * math.sqrt(N)) < 3 * se + 1e-3 * sd
+
+
+def test_sd_nmax_closed_forms():
+    """Alternating +-1: B_Nmax is 0 for even Nmax (sd 0) and +-1 for odd (sd 1).
+    Ramp b i: B_Nmax(i) = b Nmax i + const, sd = b Nmax sqrt((m^2 - 1)/12),
+    m = n - Nmax + 1 windows."""
+    alt = np.tile(np.array([1.0, -1.0], np.float32), (2, 50))
+    assert oracle.plane_sd_nmax(alt, 4)[0] == pytest.approx(0.0, abs=1e-15)
+    assert oracle.plane_sd_nmax(alt, 5)[0] == pytest.approx(1.0, rel=1e-14)
+    n, nm, b = 300, 16, 0.5
+    ramp = (b * np.arange(n, dtype=np.float64)).astype(np.float32).reshape(1, -1)
+    m = n - nm + 1
+    want = b * nm * math.sqrt((m * m - 1) / 12)
+    assert oracle.plane_sd_nmax(ramp, nm)[0] == pytest.approx(want, rel=1e-12)
+
+
+# ------------------------------------------------------------ Sec. 2.3, boxcars
+
+def test_boxcar_sums_constant_ramp_spike():
+    n = 200
+    const = np.full((2, n), 3.0, np.float32)
+    for w in (1, 2, 7, 64, 200):
+        b = oracle.boxcar_sums(const, w)
+        assert np.array_equal(b[:, : n - w + 1], np.full((2, n - w + 1), 3.0 * w))
+        assert np.isnan(b[:, n - w + 1:]).all()
+    a, s = 5.0, 2.0
+    ramp = (a + s * np.arange(n)).astype(np.float32).reshape(1, -1)
+    for w in (1, 3, 16, 50):
+        i = np.arange(n - w + 1)
+        want = w * a + s * (w * i + w * (w - 1) / 2)
+        assert np.array_equal(oracle.boxcar_sums(ramp, w)[0, : n - w + 1], want)
+    spike = np.zeros((1, n), np.float32)
+    spike[0, 100] = 9.0
+    for w in (1, 5, 33):
+        b = oracle.boxcar_sums(spike, w)[0, : n - w + 1]
+        i = np.arange(n - w + 1)
+        want = np.where((i <= 100) & (100 <= i + w - 1), 9.0, 0.0)
+        assert np.array_equal(b, want)
+
+
+def _brute_force(x, mu, sigma_by_width, widths):
+    """All (start, width) SNRs from numpy cumulative sums; the winner is the
+    first maximum over [width 1, listed widths...] (np.argmax's first index),
+    which is what a strict '>' scan in ascending width order selects."""
+    n = x.size
+    c = np.concatenate([[0.0], np.cumsum(x)])
+    cols = [1] + list(widths)
+    sig = [sigma_by_width[1]] + [sigma_by_width[w] for w in widths]
+    snr = np.full((n, len(cols)), -np.inf)
+    for k, (w, s) in enumerate(zip(cols, sig)):
+        i = np.arange(0, n - w + 1)
+        snr[i, k] = (c[i + w] - c[i] - w * mu) / s
+    arg = np.argmax(snr, axis=1)
+    return snr[np.arange(n), arg], np.array(cols)[arg]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_algorithm1_against_brute_force(seed):
+    """Tiny integer inputs with exact ties, random width subsets of 1..8."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 65))
+    x = rng.integers(-3, 4, size=(2, n)).astype(np.float32)
+    all_w = np.arange(1, 9)
+    widths = np.sort(rng.choice(all_w, size=int(rng.integers(1, 9)), replace=False))
+    mu, sd = 0.25, 1.5
+    sig = {w: math.sqrt(w) * sd for w in range(1, 9)}
+    tab = oracle.sigma_table(oracle.SIGMA_SQRTN, sd, widths)
+    best, win = oracle.boxcar_snr(x, [mu], [sd], tab, widths)
+    for r in range(2):
+        bb, ww = _brute_force(x[r].astype(np.float64), mu, sig, widths)
+        assert np.allclose(best[r], bb, rtol=1e-13, atol=1e-13)
+        assert np.array_equal(win[r], ww)
+
+
+def test_tie_rule_smallest_width_wins():
+    """x = (1, 0, 0, ...) with sigma_w = 1 for all w: every width has SNR 1 at
+    sample 0, and strict '>' keeps width 1."""
+    x = np.zeros((1, 10), np.float32)
+    x[0, 0] = 1.0
+    widths = [1, 2, 3, 4]
+    best, win = oracle.boxcar_snr(x, [0.0], [1.0], np.ones(4), widths)
+    assert best[0, 0] == 1.0 and win[0, 0] == 1
+
+
+def test_figure1_tophat_response():
+    """Figure 1: a top-hat of width W, amplitude a (mu = 0, sigma = 1) gives
+    SNR(N) = a min(N, W) / sqrt(N) at its leading sample; the best is N = W."""
+    a, n = 3.0, 256
+    widths = list(range(1, 65))
+    for W in (1, 5, 16, 40):
+        x = np.zeros((1, n), np.float32)
+        x[0, 50:50 + W] = a
+        tab = oracle.sigma_table(oracle.SIGMA_SQRTN, 1.0, widths)
+        best, win = oracle.boxcar_snr(x, [0.0], [1.0], tab, widths)
+        assert win[0, 50] == W
+        assert best[0, 50] == pytest.approx(a * math.sqrt(W), rel=1e-14)
+        for N in (1, 3, 64):
+            b = oracle.boxcar_sums(x, N)[0, 50]
+            assert b / math.sqrt(N) == pytest.approx(a * min(N, W) / math.sqrt(N))
+
+
+def test_row_end_truncates_width_set():
+    """At the last samples only widths w <= n_samp - i are evaluated."""
+    x = np.zeros((1, 8), np.float32)
+    x[0, 6:] = 5.0
+    widths = [1, 2, 4]
+    tab = oracle.sigma_table(oracle.SIGMA_SQRTN, 1.0, widths)
+    best, win = oracle.boxcar_snr(x, [0.0], [1.0], tab, widths)
+    assert win[0, 7] == 1 and best[0, 7] == 5.0
+    assert win[0, 6] == 2 and best[0, 6] == pytest.approx(10 / math.sqrt(2))
+    assert win[0, 4] == 4 and best[0, 4] == pytest.approx(10 / 2)
+
+
+# ------------------------------------------------------------ Sec. 2.4
+
+def test_threshold_inclusive():
+    thr = 6.0
+    best = np.array([[thr, np.nextafter(thr, -np.inf), thr + 1, -thr]])
+    width = np.array([[1, 2, 3, 4]], np.int32)
+    c = oracle.threshold(best, width, thr, row0=5)
+    assert list(c["sample"]) == [0, 2] and list(c["dm"]) == [5, 5]
+    assert list(c["width"]) == [1, 3]
+
+
+def test_search_finds_injected_tophats():
+    """Statistical check, not parity: the plain FP32 case's pulses are found
+    at their leading sample with SNR near the target and the matching width."""
+    import synth
+    sp = synth.plain_tophat(16, 8192, device="cpu", seed=77)
+    x = synth.to_host_numpy(sp.data)
+    cands, best, win, _ = oracle.search(x, list(range(1, 33)), 6.0)
+    for p in sp.pulses:
+        sel = cands[(cands["dm"] == p.dm) & (abs(cands["sample"] - p.sample) <= 2)]
+        assert sel.size > 0
+        top = sel[np.argmax(sel["snr"])]
+        assert abs(top["snr"] - p.snr) < 4.0
+        assert abs(int(top["width"]) - p.width) <= max(2, p.width // 3)
