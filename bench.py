@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the single-pulse search: searched DM x time samples per second.
+
+Workload (default): the SKA-like FP32 chunk -- 4096 DM trials x 524288 samples
+(33.5 s at 64 us), N(100, 12^2) noise with a +-2 sigma sinusoidal baseline
+drift of period 2^16 samples, 200 Gaussian pulses; widths 1..16 then 24..256
+in steps of 8 (46 widths); threshold 7; sigma_N = sqrt(N) sigma; one MSD for
+the whole plane.  A step is one whole search (MSD partial + merge kernels,
+then the fused boxcar / SNR / max / threshold kernel) over the plane resident
+in HBM, including the read-back of the candidate count.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl spd|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank searches its own
+plane (independent chunks, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DM×time samples/s searched and real-time factor at SKA-like size; % HBM peak"
+UNIT = "DM×time samples/s"
+WIDTHS = list(range(1, 17)) + list(range(24, 257, 8))
+THRESHOLD = 7.0
+SAMPLE_TIME_S = 64e-6
+KERNELS_PER_STEP = 5   # msd_partial, msd_merge_l1, msd_merge_final, consts, detect
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "detect_traffic.txt")
+DETECT_SRC = os.path.join(ROOT, "paper_1611_09704_gb300", "csrc", "spd_detect_kernel.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["spd", "reference"], default="spd")
+    ap.add_argument("--n-dm", type=int, default=4096)
+    ap.add_argument("--n-samp", type=int, default=524288)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=512)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def detect_source_sha() -> str:
+    with open(DETECT_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(n_samples: int, n_cand: int):
+    """DRAM bytes per detect launch from the committed ncu summary, scaled to
+    this launch; None when absent or taken on a different kernel source."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256") != detect_source_sha():
+            return None
+        read = float(kv["dram_read_bytes"]) * n_samples / float(kv["samples"])
+        write = float(kv["dram_write_bytes"]) * max(n_cand, 1) / max(float(kv["candidates"]), 1)
+        return int(read + write)
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.p = None
+        self.lines = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", sel, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], 0.0, set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"], f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_config(n_dm, n_samp, world):
+    return {"workload": (f"SKA-like FP32 chunk {n_dm} DM x {n_samp} samples (64 us), "
+                         "N(100,12^2) + 2-sigma drift + 200 Gaussian pulses; widths 1..16 + "
+                         "24..256/8 (46); f_T 7; sqrt(N) sigma; global MSD"),
+            "n_dm": n_dm, "n_samp": n_samp, "n_widths": len(WIDTHS), "threshold": THRESHOLD,
+            "dtype_in": "f32", "l2": "inputs larger than L2 (plane %.2f GB)" % (n_dm * n_samp * 4 / 1e9),
+            "parallelism": f"independent chunk per GPU x{world}"}
+
+
+# ------------------------------------------------------------------ CPU side
+
+def oracle_sample(rows, n_samp, seed):
+    """The oracle (FP64, OpenMP over rows) on `rows` rows of the SKA-like recipe."""
+    import oracle
+    import synth
+    sp = synth.ska_like(rows, n_samp, n_pulses=max(1, 200 * rows // 4096), device="cpu",
+                        seed=seed)
+    x = synth.to_host_numpy(sp.data)
+    oracle.build()
+    t0 = time.perf_counter()
+    cands, _, _, _ = oracle.search(x, WIDTHS, THRESHOLD)
+    dt = time.perf_counter() - t0
+    return dt, cands.size, oracle.num_threads()
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return 0
+    n_samp = a.n_samp
+    # calibrate the per-row cost, then size each step to fit the time budget
+    dt16, _, cores = oracle_sample(16, n_samp, 5)
+    per_row = dt16 / 16
+    rows = int(max(8, min(512, a.ref_budget_s / max(1, a.steps + a.warmup) / per_row)))
+    for w in range(a.warmup):
+        oracle_sample(rows, n_samp, 100 + w)
+    times = []
+    for k in range(a.steps):
+        dt, _, cores = oracle_sample(rows, n_samp, 1000 + k)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = rows * n_samp / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(a.n_dm, n_samp, 1),
+            "realtime_factor": n_samp * SAMPLE_TIME_S / (t * a.n_dm / rows),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} rows x {n_samp} samples per step "
+                                       "(same recipe), MSD over the sample"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU side
+
+def run_spd(a, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1611_09704_gb300 as spd
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spd.build()
+    spd.load()
+    n_dm, n_samp = a.n_dm, a.n_samp
+    n = n_dm * n_samp
+    sp = synth.ska_like(n_dm, n_samp, device=dev, seed=1611_1 + rank)
+    x = sp.data
+    cap = int(n * 0.45) + 1024
+    out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    res = torch.zeros(16, dtype=torch.uint8, device=dev)
+    msd = torch.empty(40, dtype=torch.uint8, device=dev)
+    wsb = spd.search_workspace_bytes(x, WIDTHS, THRESHOLD)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    res_host = torch.empty(16, dtype=torch.uint8, pin_memory=True)
+    stream = torch.cuda.current_stream()
+
+    def step(e0=None, e1=None, e2=None):
+        if e0 is not None:
+            e0.record(stream)
+        spd.msd(x, out=msd, workspace=ws)
+        if e1 is not None:
+            e1.record(stream)
+        spd.detect(x, msd, WIDTHS, THRESHOLD, cap, out=out, result=res, workspace=ws)
+        if e2 is not None:
+            e2.record(stream)
+        res_host.copy_(res, non_blocking=True)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    count, status = spd.read_result(res)
+    if status != 0:
+        raise RuntimeError(f"search status {status}")
+    if count > cap:
+        raise RuntimeError(f"{count} candidates exceed capacity {cap}")
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local) if rank == 0 else None
+    t_start.record(stream)
+    for k in range(a.steps):
+        step(*ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    total_ms = t_start.elapsed_time(t_end)
+    msd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    det_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / a.steps
+    value = world * n / (ms_step / 1e3)
+    if rank != 0:
+        return 0
+
+    hbm, peak_kind = peaks()
+    det_bytes = n * 4 + 16 * count
+    achieved = det_bytes / (det_ms / 1e3) / 1e9
+    traffic = recorded_traffic(n, count)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(n_dm, n_samp, world),
+            "realtime_factor": n_samp * SAMPLE_TIME_S / (ms_step / 1e3),
+            "candidates_per_step": count,
+            "roofline": {"bound": "hbm", "kernel": "detect (boxcar+SNR+max+threshold)",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "algorithmic_bytes": det_bytes, "ms": det_ms},
+            "step_breakdown_ms": {"msd": msd_ms, "detect": det_ms},
+            "whole_step_hbm_frac": (2 * n * 4 + 16 * count) / (ms_step / 1e3) / 1e9 / hbm,
+            "gpu_launches": KERNELS_PER_STEP * a.steps,
+            "clocks": clocks}
+
+    if not a.no_e2e:
+        line["e2e"] = e2e(spd, x, out, res, msd, ws, cap, count, a.e2e_steps, n, dev)
+    if not a.no_cpu_baseline:
+        rows = min(a.cpu_rows, n_dm)
+        dt, _, cores = oracle_sample(rows, n_samp, 7)
+        line["cpu_baseline"] = {"value": rows * n_samp / dt, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{rows} rows x {n_samp} samples of the same recipe, "
+                                          f"oracle MSD over the sample, {dt:.1f} s"}
+    print(json.dumps(line))
+    return 0
+
+
+def e2e(spd, x, out, res, msd, ws, cap, count, steps, n, dev):
+    """spd_search from pinned host memory: H2D of the plane, the search, D2H of
+    the count and of every candidate record, per step."""
+    import torch
+    xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    xh.copy_(x)
+    ch = torch.empty((max(count, 1), 4), dtype=torch.int32, pin_memory=True)
+    rh = torch.empty(16, dtype=torch.uint8, pin_memory=True)
+    times, d2h = [], []
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.copy_(xh, non_blocking=True)
+        spd.search(x, WIDTHS, THRESHOLD, cap, out=out, result=res, msd_out=msd, workspace=ws)
+        rh.copy_(res, non_blocking=True)
+        torch.cuda.synchronize()
+        c = int(rh[:8].numpy().view("<u8")[0])
+        m = min(c, cap, ch.shape[0])
+        ch[:m].copy_(out[:m], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if k:
+            times.append(dt)
+            d2h.append(16 + 16 * m)
+    t = sum(times) / len(times)
+    return {"value": n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
+            "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3,
+            "api": "spd_search (C ABI) with pinned host buffers"}
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    rc = run_spd(a, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * spd.h -- C ABI of libspd, a GB300 (sm_103a) single-pulse search over
+ * de-dispersed data laid out as DM trials x time samples, after Adamek &
+ * Armour, "A Real-time Single Pulse Detection Algorithm for GPUs"
+ * (arXiv:1611.09704).
+ *
+ * The search has four steps:
+ *   (a) mean mu and standard deviation sigma of the data with Chan's streaming
+ *       update (Eq. 1) and pairwise merge (Eq. 2), as a block-partial kernel
+ *       followed by a merge kernel (Sec. 2.1);
+ *   (b) boxcar filters of the listed widths at every sample (Sec. 2.3);
+ *   (c) SNR = (B_w - w mu) / sigma_w with sigma_w from Eq. 4 or Eq. 5
+ *       (Sec. 2.2), keeping per sample the highest SNR and its width
+ *       (Algorithm 1, strict ">" so the smallest width wins ties);
+ *   (d) candidates with SNR >= threshold, compacted into an unordered list of
+ *       (DM, sample, SNR, width) records (Sec. 2.4).
+ *
+ * Conventions shared by every call:
+ *   - Pointers named *_dev, and plane data, are device pointers; everything
+ *     else (structs passed by pointer, width lists) lives on the host and is
+ *     read before the call returns.  The caller owns all memory; the library
+ *     never allocates device memory and keeps no pointer after a call returns.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL means the legacy default stream).  Arguments are validated on the
+ *     host before anything is launched; a failed validation launches nothing.
+ *   - Results that depend on data (degenerate sigma, number of candidates)
+ *     are written to device memory and become visible after the caller
+ *     synchronises the stream.  Nothing is thrown across the ABI.
+ *   - Sample windows are forward: B_w(i) = x[i] + ... + x[i+w-1].  Near the
+ *     end of a row only widths w <= n_samp - i are evaluated; width 1 is always
+ *     evaluated.  Candidates carry the start sample i.
+ *   - Widths: strictly ascending, 1 <= w <= SPD_MAX_WIDTH, at most
+ *     SPD_MAX_WIDTHS of them.
+ */
+#ifndef SPD_H
+#define SPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPD_VERSION 100
+#define SPD_MAX_WIDTH 4096
+#define SPD_MAX_WIDTHS 4096
+
+typedef enum {
+    SPD_OK = 0,
+    SPD_ERR_INVALID_ARG = 1,      /* bad pointer, size, width list or mode */
+    SPD_ERR_CUDA = 2,             /* a CUDA call or launch failed; see spd_last_cuda_error */
+    SPD_ERR_NO_MEMORY = 3,        /* the workspace passed is smaller than required */
+    SPD_ERR_OVERFLOW = 4,         /* more candidates than capacity (reported by the host) */
+    SPD_ERR_DEGENERATE_SIGMA = 5, /* sigma <= 0 or not finite: no SNR is defined */
+    SPD_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    SPD_ERR_UNSUPPORTED = 7       /* valid request this build cannot serve */
+} spd_status;
+
+typedef enum { SPD_F32 = 0, SPD_F16 = 1, SPD_BF16 = 2 } spd_dtype;
+
+/* sigma_w after a w-sample boxcar (Sec. 2.2):
+ *   SQRTN          Eq. 4: sqrt(w) sigma
+ *   LINEAR         Eq. 5 as printed: sqrt(w) sigma + (w-1) sigma_Nmax/(Nmax-1)
+ *   LINEAR_EXCESS  Eq. 5 read as the linear excess over Eq. 4, exact at w = 1
+ *                  and w = Nmax: sqrt(w) sigma
+ *                                + (w-1)(sigma_Nmax - sqrt(Nmax) sigma)/(Nmax-1)
+ * sigma_Nmax is the measured standard deviation of the Nmax-sample boxcar
+ * series over full windows (Sec. 2.2). */
+typedef enum {
+    SPD_SIGMA_SQRTN = 0,
+    SPD_SIGMA_LINEAR = 1,
+    SPD_SIGMA_LINEAR_EXCESS = 2
+} spd_sigma_mode;
+
+/* Which samples one (mu, sigma) describes: the whole plane of the call, as in
+ * Sec. 2.1 ("for the dataset"), or each DM row on its own. */
+typedef enum { SPD_MSD_GLOBAL = 0, SPD_MSD_PER_ROW = 1 } spd_msd_scope;
+
+/* A DM x time plane in device memory, row-major: element (r, t) is at
+ * data + (r * row_stride + t) * sizeof(element), 0 <= t < n_samp <= row_stride.
+ * F16 / BF16 data may carry an FP32 per-row scale and offset (device arrays of
+ * n_dm floats, either may be NULL); the value searched is
+ * fmaf(scale[r], q, offset[r]) computed in FP32 (scale NULL: q itself). */
+typedef struct {
+    const void *data;
+    int32_t dtype;            /* spd_dtype */
+    int32_t reserved0;
+    int64_t n_dm;
+    int64_t n_samp;
+    int64_t row_stride;       /* in elements */
+    const float *row_scale;   /* device, n_dm entries, or NULL */
+    const float *row_offset;  /* device, n_dm entries, or NULL */
+} spd_plane;
+
+/* Result of step (a) for one scope entry (40 bytes).  n: samples described;
+ * sd_nmax: sigma_Nmax of Eq. 5 (0 when not measured); status: SPD_OK or
+ * SPD_ERR_DEGENERATE_SIGMA. */
+typedef struct {
+    double mean;
+    double sd;
+    double sd_nmax;
+    int64_t n;
+    int32_t nmax;
+    int32_t status;
+} spd_msd_stats;
+
+/* One candidate (16 bytes): DM row, start sample, highest SNR, its width. */
+typedef struct {
+    int32_t dm;
+    int32_t sample;
+    float snr;
+    int32_t width;
+} spd_candidate;
+
+/* Device-side summary written by the candidate-producing calls (16 bytes).
+ * count: exact number of samples with SNR >= threshold, even when it exceeds
+ * the capacity (then only `capacity` records are written, which ones is
+ * unspecified); status: SPD_OK or SPD_ERR_DEGENERATE_SIGMA. */
+typedef struct {
+    uint64_t count;
+    int32_t status;
+    int32_t reserved0;
+} spd_result;
+
+/* Parameters of the search (host struct; `widths` is a host array). */
+typedef struct {
+    const int32_t *widths;
+    int32_t n_widths;
+    float threshold;          /* f_T of Sec. 2.4, in SNR units */
+    int32_t sigma_mode;       /* spd_sigma_mode */
+    int32_t msd_scope;        /* spd_msd_scope */
+    int32_t nmax_sigma;       /* Nmax of Eq. 5; 0 = last listed width */
+    int32_t reserved0;
+} spd_search_params;
+
+/* ------------------------------------------------------------------------ */
+
+int32_t spd_version(void);
+const char *spd_status_string(int32_t status);
+/* cudaError_t of the most recent SPD_ERR_CUDA on the calling thread (0 if none). */
+int32_t spd_last_cuda_error(void);
+
+/* Bytes of device workspace spd_msd needs (256-byte aligned base). */
+size_t spd_msd_workspace_bytes(const spd_plane *plane, int32_t scope, int32_t nmax_sigma);
+
+/* Step (a), Sec. 2.1, Eq. 1-2 (and the sigma_Nmax of Sec. 2.2 when
+ * nmax_sigma >= 2).  A block-partial kernel gives (n, T, S) of equal-sized
+ * pieces of each row (Eq. 1 per thread in FP32 with compensated sums, Eq. 2
+ * across lanes, warps and the block); a merge kernel adds the pieces with
+ * Eq. 2 in FP64 in a fixed order, so the result is deterministic.
+ *   out_dev: device array of 1 (GLOBAL) or n_dm (PER_ROW) spd_msd_stats.
+ *   nmax_sigma: 0 skips sigma_Nmax; >= 2 also measures the sd of the
+ *     nmax-sample boxcar series over full windows (rows shorter than nmax
+ *     contribute nothing).
+ * Errors: SPD_ERR_INVALID_ARG (bad plane/scope/nmax), SPD_ERR_NO_MEMORY
+ * (workspace too small), SPD_ERR_CUDA.  An empty plane (n_dm or n_samp 0)
+ * yields n = 0 and status SPD_ERR_DEGENERATE_SIGMA; so does sigma <= 0. */
+spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
+                   spd_msd_stats *out_dev, void *workspace, size_t workspace_bytes,
+                   void *stream);
+
+/* Bytes of device workspace spd_boxcar_snr needs. */
+size_t spd_boxcar_snr_workspace_bytes(const spd_plane *plane, int32_t scope,
+                                      const int32_t *widths, int32_t n_widths);
+
+/* Steps (b)+(c), Sec. 2.3, Algorithm 1: for every sample of every row, the
+ * highest SNR over width 1 and the listed widths and the width that gave it.
+ *   msd_dev: the spd_msd_stats array of `scope` (from spd_msd, or filled by the
+ *     caller; sd_nmax is used by the LINEAR modes, with nmax_sigma = its nmax).
+ *   snr_out: float [n_dm][out_stride]; width_out: uint16 [n_dm][out_stride]
+ *     (device; columns >= n_samp are not written).
+ * SNRs are exact up to FP32 rounding plus a relative 2^-17 quantisation used
+ * to carry the width index through the max; widths whose SNRs differ by less
+ * than that are treated as ties.  A degenerate MSD entry leaves its rows'
+ * outputs at NaN / 0.
+ * Errors: SPD_ERR_INVALID_ARG, SPD_ERR_NO_MEMORY, SPD_ERR_CUDA. */
+spd_status spd_boxcar_snr(const spd_plane *plane, const spd_msd_stats *msd_dev, int32_t scope,
+                          const int32_t *widths, int32_t n_widths, int32_t sigma_mode,
+                          float *snr_out, uint16_t *width_out, int64_t out_stride,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/* Step (d), Sec. 2.4: every (dm, t) with snr[dm][t] >= threshold becomes a
+ * record; records are appended in no particular order with warp- and
+ * block-aggregated atomics.  snr, width: device planes [n_dm][stride].
+ * out: device array of `capacity` records (may be NULL when capacity is 0).
+ * result_dev->count is set to the exact number found (the call zeroes it
+ * first).  Errors: SPD_ERR_INVALID_ARG, SPD_ERR_CUDA. */
+spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int64_t n_dm,
+                                    int64_t n_samp, int64_t stride, float threshold,
+                                    spd_candidate *out, int64_t capacity,
+                                    spd_result *result_dev, void *stream);
+
+/* Bytes of device workspace spd_detect / spd_search need. */
+size_t spd_detect_workspace_bytes(const spd_plane *plane, const spd_search_params *params);
+size_t spd_search_workspace_bytes(const spd_plane *plane, const spd_search_params *params);
+
+/* Steps (b)+(c)+(d) fused in one kernel given the MSD (msd_dev as for
+ * spd_boxcar_snr): boxcars, SNR, max over widths and thresholding happen in
+ * registers and shared memory; only candidate records leave the SM.  The
+ * candidate set equals thresholding spd_boxcar_snr's output.
+ * Errors: as spd_boxcar_snr, plus result semantics as spd_threshold_candidates. */
+spd_status spd_detect(const spd_plane *plane, const spd_search_params *params,
+                      const spd_msd_stats *msd_dev, spd_candidate *out, int64_t capacity,
+                      spd_result *result_dev, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
+/* The whole path: spd_msd (a) then spd_detect (b, c, d) on one stream.
+ *   msd_out_dev: optional device array (1 or n_dm entries) receiving the MSD;
+ *     NULL keeps it inside the workspace.
+ * The plane is read twice from HBM: once for the MSD, once for the search,
+ * because no SNR is known before the dataset's sigma is (Sec. 2.1 -> 2.3). */
+spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
+                      spd_candidate *out, int64_t capacity, spd_result *result_dev,
+                      spd_msd_stats *msd_out_dev, void *workspace, size_t workspace_bytes,
+                      void *stream);
+
+/* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
+ * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */
+spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out,
+                           int64_t out_stride, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPD_H */

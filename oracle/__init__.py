@@ -76,6 +76,8 @@ def _load():
     lib.oracle_threshold.restype = I64
     lib.oracle_dequant_row.argtypes = [P, I32, I64, P, P, I64, I64, P]
     lib.oracle_num_threads.restype = I32
+    lib.oracle_snr_at.argtypes = [P, I32, I64, I64, P, P, I64, I64, I32, D, D]
+    lib.oracle_snr_at.restype = D
     _lib = lib
     return lib
 
@@ -243,6 +245,14 @@ def boxcar_snr(plane, mean, sd, sigma_tab, widths, scope: int = SCOPE_GLOBAL,
     if rc:
         raise ValueError(f"oracle_boxcar_snr rc={rc}")
     return best, win
+
+
+def snr_at(plane, row: int, sample: int, width: int, mean: float, sigma_w: float) -> float:
+    """(B_w(i) - w mu) / sigma_w for one (row, start, width), NaN past the row end."""
+    p = as_plane(plane)
+    return float(_load().oracle_snr_at(_ptr(p.data), _DTYPES[p.dtype], p.n_samp, p.stride,
+                                       _ptr(p.scale), _ptr(p.offset), int(row), int(sample),
+                                       int(width), float(mean), float(sigma_w)))
 
 
 # ----------------------------------------------------------------- Sec. 2.4

@@ -430,3 +430,17 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* SNR of one (row, start, width) pair, Sec. 2.3: (B_w(i) - w mu) / sigma_w with
+ * B_w(i) summed directly in FP64.  NaN when the window passes the row end.
+ * Used to check that a reported width is one of the (near-)tied maxima. */
+double oracle_snr_at(const void *data, int dtype, int64_t n_samp, int64_t stride,
+                     const float *scale, const float *offset, int64_t r, int64_t i,
+                     int w, double mean, double sigma_w)
+{
+    if (i < 0 || w < 1 || i + w > n_samp) return NAN;
+    double b = 0.0;
+    for (int k = 0; k < w; ++k)
+        b += sample_value(data, dtype, stride, scale, offset, r, i + k);
+    return (b - (double)w * mean) / sigma_w;
+}

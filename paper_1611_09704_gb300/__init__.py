@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) single-pulse search over de-dispersed DM x time planes,
+after Adamek & Armour, arXiv:1611.09704.
+
+The search runs in the CUDA kernels of ``_build/libspd.so`` behind the C ABI
+of ``include/spd.h``; :mod:`.binding` marshals torch tensors into those calls.
+Build the library with :func:`build`.
+"""
+from .builder import build, LIB as LIBRARY_PATH  # noqa: F401
+from .binding import (  # noqa: F401
+    BF16, F16, F32, MSD_GLOBAL, MSD_PER_ROW, SIGMA_LINEAR, SIGMA_LINEAR_EXCESS, SIGMA_SQRTN,
+    CAND_DTYPE, MSD_DTYPE, Plane, SpdError, boxcar_snr, boxcar_sums, candidates_to_numpy,
+    detect, load, msd, msd_to_numpy, read_result, search, search_workspace_bytes,
+    threshold_candidates, widths_to_numpy)

@@ -1,0 +1,346 @@
+"""ctypes binding of libspd (include/spd.h): argument marshalling only.
+
+Every function here has the name of the C call it wraps (without the ``spd_``
+prefix), takes torch tensors that already live on the GPU, allocates the
+workspace the call asks for with torch, and raises :class:`SpdError` on a
+non-zero status.  All arithmetic of the search runs in the CUDA kernels of
+``_build/libspd.so``; if that library is missing this module raises instead of
+computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import builder as _build
+
+# ----------------------------------------------------------------- ABI types
+
+SPD_OK, SPD_ERR_INVALID_ARG, SPD_ERR_CUDA, SPD_ERR_NO_MEMORY = 0, 1, 2, 3
+SPD_ERR_OVERFLOW, SPD_ERR_DEGENERATE_SIGMA, SPD_ERR_TIMEOUT, SPD_ERR_UNSUPPORTED = 4, 5, 6, 7
+F32, F16, BF16 = 0, 1, 2
+SIGMA_SQRTN, SIGMA_LINEAR, SIGMA_LINEAR_EXCESS = 0, 1, 2
+MSD_GLOBAL, MSD_PER_ROW = 0, 1
+
+
+class SpdPlane(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("n_dm", ctypes.c_int64),
+                ("n_samp", ctypes.c_int64), ("row_stride", ctypes.c_int64),
+                ("row_scale", ctypes.c_void_p), ("row_offset", ctypes.c_void_p)]
+
+
+class SpdMsdStats(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_double), ("sd", ctypes.c_double),
+                ("sd_nmax", ctypes.c_double), ("n", ctypes.c_int64),
+                ("nmax", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class SpdCandidate(ctypes.Structure):
+    _fields_ = [("dm", ctypes.c_int32), ("sample", ctypes.c_int32),
+                ("snr", ctypes.c_float), ("width", ctypes.c_int32)]
+
+
+class SpdResult(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+
+class SpdSearchParams(ctypes.Structure):
+    _fields_ = [("widths", ctypes.POINTER(ctypes.c_int32)), ("n_widths", ctypes.c_int32),
+                ("threshold", ctypes.c_float), ("sigma_mode", ctypes.c_int32),
+                ("msd_scope", ctypes.c_int32), ("nmax_sigma", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
+
+
+MSD_BYTES = ctypes.sizeof(SpdMsdStats)      # 40
+CAND_BYTES = ctypes.sizeof(SpdCandidate)    # 16
+RESULT_BYTES = ctypes.sizeof(SpdResult)     # 16
+
+MSD_DTYPE = np.dtype([("mean", "<f8"), ("sd", "<f8"), ("sd_nmax", "<f8"), ("n", "<i8"),
+                      ("nmax", "<i4"), ("status", "<i4")])
+CAND_DTYPE = np.dtype([("dm", "<i4"), ("sample", "<i4"), ("snr", "<f4"), ("width", "<i4")])
+
+# Every symbol include/spd.h declares, for the export check.
+EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
+           "spd_msd_workspace_bytes", "spd_msd", "spd_boxcar_snr_workspace_bytes",
+           "spd_boxcar_snr", "spd_threshold_candidates", "spd_detect_workspace_bytes",
+           "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums"]
+
+
+class SpdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        lib = _lib
+        msg = lib.spd_status_string(status).decode() if lib else str(status)
+        extra = ""
+        if lib is not None and status == SPD_ERR_CUDA:
+            extra = f" (cudaError {lib.spd_last_cuda_error()})"
+        super().__init__(f"{what}: {msg}{extra}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libspd.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libspd is not built ({path} missing); run "
+                           "paper_1611_09704_gb300.build() first")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, SZ, F = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t,
+                          ctypes.c_float)
+    pp = ctypes.POINTER(SpdPlane)
+    pq = ctypes.POINTER(SpdSearchParams)
+    lib.spd_version.restype = I32
+    lib.spd_status_string.argtypes = [I32]
+    lib.spd_status_string.restype = ctypes.c_char_p
+    lib.spd_last_cuda_error.restype = I32
+    lib.spd_msd_workspace_bytes.argtypes = [pp, I32, I32]
+    lib.spd_msd_workspace_bytes.restype = SZ
+    lib.spd_msd.argtypes = [pp, I32, I32, P, P, SZ, P]
+    lib.spd_msd.restype = I32
+    lib.spd_boxcar_snr_workspace_bytes.argtypes = [pp, I32, P, I32]
+    lib.spd_boxcar_snr_workspace_bytes.restype = SZ
+    lib.spd_boxcar_snr.argtypes = [pp, P, I32, P, I32, I32, P, P, I64, P, SZ, P]
+    lib.spd_boxcar_snr.restype = I32
+    lib.spd_threshold_candidates.argtypes = [P, P, I64, I64, I64, F, P, I64, P, P]
+    lib.spd_threshold_candidates.restype = I32
+    lib.spd_detect_workspace_bytes.argtypes = [pp, pq]
+    lib.spd_detect_workspace_bytes.restype = SZ
+    lib.spd_search_workspace_bytes.argtypes = [pp, pq]
+    lib.spd_search_workspace_bytes.restype = SZ
+    lib.spd_detect.argtypes = [pp, pq, P, P, I64, P, P, SZ, P]
+    lib.spd_detect.restype = I32
+    lib.spd_search.argtypes = [pp, pq, P, I64, P, P, P, SZ, P]
+    lib.spd_search.restype = I32
+    lib.spd_boxcar_sums.argtypes = [pp, I32, P, I64, P]
+    lib.spd_boxcar_sums.restype = I32
+    _lib = lib
+    return lib
+
+
+def _check(status: int, what: str):
+    if status != SPD_OK:
+        raise SpdError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+_DT = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+
+
+@dataclass
+class Plane:
+    """A device plane: ``data`` [n_dm, row_stride] (float32 / float16 / bfloat16,
+    row-major, unit stride along time); ``n_samp`` valid samples per row;
+    optional float32 per-row ``scale`` / ``offset``."""
+    data: torch.Tensor
+    n_samp: int | None = None
+    scale: torch.Tensor | None = None
+    offset: torch.Tensor | None = None
+
+    def __post_init__(self):
+        if self.data.dtype not in _DT:
+            raise TypeError(f"plane dtype {self.data.dtype} not supported")
+        if self.data.dim() != 2 or self.data.stride(1) != 1:
+            raise ValueError("plane must be 2-D with unit stride along time")
+        if self.n_samp is None:
+            self.n_samp = self.data.shape[1]
+
+    @property
+    def n_dm(self):
+        return self.data.shape[0]
+
+    def c(self) -> SpdPlane:
+        d = self.data
+        return SpdPlane(d.data_ptr() if d.numel() else 0, _DT[d.dtype], 0, d.shape[0],
+                        self.n_samp, d.stride(0) if d.shape[0] else self.n_samp,
+                        self.scale.data_ptr() if self.scale is not None else None,
+                        self.offset.data_ptr() if self.offset is not None else None)
+
+
+def as_plane(x, **kw) -> Plane:
+    return x if isinstance(x, Plane) else Plane(x, **kw)
+
+
+def _params(widths, threshold, sigma_mode, scope, nmax_sigma):
+    w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    p = SpdSearchParams(w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), w.size,
+                        float(threshold), int(sigma_mode), int(scope), int(nmax_sigma), 0)
+    return p, w
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # 256-byte aligned: torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def entries(plane: Plane, scope: int) -> int:
+    return plane.n_dm if scope == MSD_PER_ROW else 1
+
+
+# --------------------------------------------------------------------- calls
+
+def msd(x, scope=MSD_GLOBAL, nmax_sigma=0, *, stream=None, out=None, workspace=None,
+        **kw) -> torch.Tensor:
+    """spd_msd: returns a uint8 device tensor holding 1 or n_dm spd_msd_stats."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    n = entries(pl, scope)
+    if out is None:
+        out = torch.empty(max(n, 1) * MSD_BYTES, dtype=torch.uint8, device=pl.data.device)
+    wsb = lib.spd_msd_workspace_bytes(ctypes.byref(cp), scope, nmax_sigma)
+    ws = workspace if workspace is not None else _workspace(wsb, pl.data.device)
+    _check(lib.spd_msd(ctypes.byref(cp), scope, nmax_sigma, _ptr(out), _ptr(ws), wsb,
+                       _stream(stream)), "spd_msd")
+    return out
+
+
+def msd_to_numpy(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(MSD_DTYPE)
+
+
+def boxcar_snr(x, msd_dev, widths, sigma_mode=SIGMA_SQRTN, scope=MSD_GLOBAL, *, stream=None,
+               snr_out=None, width_out=None, **kw):
+    """spd_boxcar_snr: (snr float32 [n_dm, n_samp], width int16 [n_dm, n_samp]
+    holding uint16 widths)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    dev = pl.data.device
+    if snr_out is None:
+        snr_out = torch.empty((pl.n_dm, pl.n_samp), dtype=torch.float32, device=dev)
+    if width_out is None:
+        width_out = torch.empty((pl.n_dm, pl.n_samp), dtype=torch.int16, device=dev)
+    wsb = lib.spd_boxcar_snr_workspace_bytes(ctypes.byref(cp), scope, w.ctypes.data, w.size)
+    ws = _workspace(wsb, dev)
+    _check(lib.spd_boxcar_snr(ctypes.byref(cp), _ptr(msd_dev), scope, w.ctypes.data, w.size,
+                              sigma_mode, _ptr(snr_out), _ptr(width_out), snr_out.stride(0),
+                              _ptr(ws), wsb, _stream(stream)), "spd_boxcar_snr")
+    return snr_out, width_out
+
+
+def threshold_candidates(snr, width, threshold, capacity, *, n_samp=None, stream=None,
+                         out=None, result=None):
+    """spd_threshold_candidates: (records int32 [capacity, 4], result uint8 [16])."""
+    lib = load()
+    dev = snr.device
+    n_dm, n = snr.shape[0], (snr.shape[1] if n_samp is None else n_samp)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 4), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    _check(lib.spd_threshold_candidates(_ptr(snr), _ptr(width), n_dm, n, snr.stride(0),
+                                        float(threshold), _ptr(out), int(capacity),
+                                        _ptr(result), _stream(stream)),
+           "spd_threshold_candidates")
+    return out, result
+
+
+def detect(x, msd_dev, widths, threshold, capacity, sigma_mode=SIGMA_SQRTN, scope=MSD_GLOBAL,
+           nmax_sigma=0, *, stream=None, out=None, result=None, workspace=None, **kw):
+    """spd_detect (steps b-d given the MSD): (records, result)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    dev = pl.data.device
+    prm, keep = _params(widths, threshold, sigma_mode, scope, nmax_sigma)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 4), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    wsb = lib.spd_detect_workspace_bytes(ctypes.byref(cp), ctypes.byref(prm))
+    ws = workspace if workspace is not None else _workspace(wsb, dev)
+    _check(lib.spd_detect(ctypes.byref(cp), ctypes.byref(prm), _ptr(msd_dev), _ptr(out),
+                          int(capacity), _ptr(result), _ptr(ws), wsb, _stream(stream)),
+           "spd_detect")
+    del keep
+    return out, result
+
+
+def search_workspace_bytes(x, widths, threshold=0.0, sigma_mode=SIGMA_SQRTN,
+                           scope=MSD_GLOBAL, nmax_sigma=0, **kw) -> int:
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    prm, keep = _params(widths, threshold, sigma_mode, scope, nmax_sigma)
+    return int(lib.spd_search_workspace_bytes(ctypes.byref(cp), ctypes.byref(prm)))
+
+
+def search(x, widths, threshold, capacity, sigma_mode=SIGMA_SQRTN, scope=MSD_GLOBAL,
+           nmax_sigma=0, *, stream=None, out=None, result=None, msd_out=None,
+           workspace=None, **kw):
+    """spd_search (the whole path): (records int32 [capacity, 4], result, msd)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    dev = pl.data.device
+    prm, keep = _params(widths, threshold, sigma_mode, scope, nmax_sigma)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 4), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    if msd_out is None:
+        msd_out = torch.empty(max(entries(pl, scope), 1) * MSD_BYTES, dtype=torch.uint8,
+                              device=dev)
+    wsb = lib.spd_search_workspace_bytes(ctypes.byref(cp), ctypes.byref(prm))
+    ws = workspace if workspace is not None else _workspace(wsb, dev)
+    _check(lib.spd_search(ctypes.byref(cp), ctypes.byref(prm), _ptr(out), int(capacity),
+                          _ptr(result), _ptr(msd_out), _ptr(ws), wsb, _stream(stream)),
+           "spd_search")
+    del keep
+    return out, result, msd_out
+
+
+def boxcar_sums(x, w, *, stream=None, out=None, **kw):
+    """spd_boxcar_sums: raw B_w(i), NaN past the row end."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    if out is None:
+        out = torch.empty((pl.n_dm, pl.n_samp), dtype=torch.float32, device=pl.data.device)
+    _check(lib.spd_boxcar_sums(ctypes.byref(cp), int(w), _ptr(out), out.stride(0),
+                               _stream(stream)), "spd_boxcar_sums")
+    return out
+
+
+# ------------------------------------------------------------------ decoding
+
+def read_result(result: torch.Tensor) -> tuple[int, int]:
+    """(count, status) of a device spd_result (synchronises)."""
+    r = result.detach().cpu().numpy()
+    return int(r[:8].view(np.uint64)[0]), int(r[8:12].view(np.int32)[0])
+
+
+def candidates_to_numpy(out: torch.Tensor, count: int) -> np.ndarray:
+    n = min(int(count), out.shape[0])
+    return out[:n].detach().cpu().numpy().view(CAND_DTYPE).reshape(-1)
+
+
+def widths_to_numpy(width: torch.Tensor) -> np.ndarray:
+    return width.detach().cpu().numpy().view(np.uint16).astype(np.int32)

@@ -1,0 +1,449 @@
+// spd_api.cu -- host side of the C ABI declared in include/spd.h: argument
+// validation, the width program (how the running boxcar sums grow from one
+// listed width to the next), workspace layout and kernel launches.
+#include "spd_internal.cuh"
+
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <vector>
+
+using namespace spd;
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+spd_status cuda_fail(cudaError_t e) {
+    g_last_cuda_error = (int)e;
+    return SPD_ERR_CUDA;
+}
+
+#define SPD_CK(x)                                        \
+    do {                                                 \
+        cudaError_t e_ = (x);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_);     \
+    } while (0)
+
+#define SPD_TRY(x)                                       \
+    do {                                                 \
+        spd_status s_ = (x);                             \
+        if (s_ != SPD_OK) return s_;                     \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool plane_empty(const spd_plane *p) { return p->n_dm == 0 || p->n_samp == 0; }
+
+spd_status check_plane(const spd_plane *p) {
+    if (!p) return SPD_ERR_INVALID_ARG;
+    if (p->dtype < SPD_F32 || p->dtype > SPD_BF16) return SPD_ERR_INVALID_ARG;
+    if (p->n_dm < 0 || p->n_samp < 0) return SPD_ERR_INVALID_ARG;
+    if (p->n_dm > INT32_MAX || p->n_samp > INT32_MAX) return SPD_ERR_INVALID_ARG;
+    if (plane_empty(p)) return SPD_OK;
+    if (!p->data || p->row_stride < p->n_samp) return SPD_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(p->data) % elem_bytes(p->dtype)) return SPD_ERR_INVALID_ARG;
+    if (p->row_offset && !p->row_scale) return SPD_ERR_INVALID_ARG;
+    return SPD_OK;
+}
+
+int plane_vec_ok(const spd_plane *p) {
+    const size_t eb = elem_bytes(p->dtype);
+    const size_t need = 4 * eb;   // four elements per vector load
+    return (reinterpret_cast<uintptr_t>(p->data) % need == 0) &&
+           ((size_t)p->row_stride * eb) % need == 0;
+}
+
+int64_t entries_of(const spd_plane *p, int scope) { return scope == SPD_MSD_PER_ROW ? p->n_dm : 1; }
+
+bool scope_ok(int scope) { return scope == SPD_MSD_GLOBAL || scope == SPD_MSD_PER_ROW; }
+
+// ------------------------------------------------------------ MSD workspace
+
+struct MsdLayout {
+    int64_t upr;           // units per row
+    size_t parts_off, scratch_off, total;
+};
+constexpr int kMergeScratch = 256;
+
+MsdLayout msd_layout(const spd_plane *p) {
+    MsdLayout l;
+    l.upr = p->n_samp > 0 ? (p->n_samp + kMsdUnit - 1) / kMsdUnit : 0;
+    const size_t parts = (size_t)(p->n_dm * l.upr) * sizeof(MsdPart);
+    l.parts_off = 0;
+    l.scratch_off = align_up(parts);
+    l.total = l.scratch_off + align_up(kMergeScratch * sizeof(MsdPart));
+    return l;
+}
+
+// ----------------------------------------------------------- width program
+
+// Evaluated widths are width 1 (the starting value of Algorithm 1) followed
+// by the listed widths.  Between consecutive evaluated widths the running sum
+// grows by d samples: q steps of a G-sample window sum and r single samples
+// (d = qG + r), the last step completing the width.  Steps are grouped into
+// runs of one kind.  G is chosen to minimise the number of steps.
+spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
+    if (!widths || n < 1 || n > SPD_MAX_WIDTHS) return SPD_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        if (widths[k] < 1 || widths[k] > SPD_MAX_WIDTH) return SPD_ERR_INVALID_ARG;
+        if (k && widths[k] <= widths[k - 1]) return SPD_ERR_INVALID_ARG;
+    }
+    std::vector<int> E;
+    if (widths[0] != 1) E.push_back(1);
+    for (int k = 0; k < n; ++k) E.push_back(widths[k]);
+    const int ne = (int)E.size();
+
+    auto cost = [&](int g) {
+        long c = 0;
+        for (int k = 1; k < ne; ++k) {
+            const int d = E[k] - E[k - 1];
+            c += g ? d / g + d % g : d;
+        }
+        return c + (g ? 4 : 0);   // building S_G costs about a few steps per sample
+    };
+    int G = 0;
+    long best = cost(0);
+    for (int g : {4, 8, 16}) {
+        const long c = cost(g);
+        if (c < best) { best = c; G = g; }
+    }
+
+    struct Step { int src, pos, eval, widx; };
+    std::vector<Step> steps;
+    steps.push_back({0, 0, 1, 0});
+    int pos = 1;
+    for (int k = 1; k < ne; ++k) {
+        const int d = E[k] - E[k - 1];
+        const int q = G ? d / G : 0;
+        const int r = G ? d % G : d;
+        for (int j = 0; j < q; ++j) { steps.push_back({1, pos, 0, -1}); pos += G; }
+        for (int j = 0; j < r; ++j) { steps.push_back({0, pos, 0, -1}); pos += 1; }
+        steps.back().eval = 1;
+        steps.back().widx = k;
+    }
+
+    std::vector<Run> runs;
+    std::vector<int> rstride;
+    for (const Step &s : steps) {
+        const int stride = s.src ? G : 1;
+        if (!runs.empty()) {
+            Run &b = runs.back();
+            const int bsrc = (b.flags & kRunSrcG) ? 1 : 0;
+            const int beval = (b.flags & kRunEval) ? 1 : 0;
+            const bool same = bsrc == s.src && beval == s.eval &&
+                              b.off + b.count * rstride.back() == s.pos && b.count < 32000 &&
+                              (!s.eval || ((b.widx0 >> 6) == (s.widx >> 6)));
+            if (same) { b.count++; continue; }
+        }
+        Run r;
+        r.off = (int16_t)s.pos;
+        r.count = 1;
+        r.widx0 = (int16_t)(s.eval ? s.widx : 0);
+        r.flags = (uint16_t)((s.src ? kRunSrcG : 0) | (s.eval ? kRunEval : 0));
+        runs.push_back(r);
+        rstride.push_back(stride);
+    }
+    for (Run &r : runs) {
+        if (!(r.flags & kRunEval)) continue;
+        const int last = r.widx0 + r.count - 1;
+        if ((last & 63) == 63 || last == ne - 1) r.flags |= kRunEndGroup;
+    }
+    if ((int)runs.size() > kMaxRuns) return SPD_ERR_UNSUPPORTED;
+
+    memset(&prog, 0, sizeof(prog));
+    prog.n_runs = (int)runs.size();
+    prog.n_eval = ne;
+    prog.wmax = E.back();
+    prog.G = G;
+    for (size_t i = 0; i < runs.size(); ++i) prog.runs[i] = runs[i];
+    for (int k = 0; k < ne; ++k) prog.eval_w[k] = (uint16_t)E[k];
+    return SPD_OK;
+}
+
+int program_R(const Program &prog) { return (kTile + prog.wmax + 32 + 15) / 16 + 1; }
+
+size_t program_smem(const Program &prog) {
+    const int R = program_R(prog);
+    const size_t arrays = (size_t)(prog.G ? 2 : 1) * kX * R * sizeof(float);
+    return arrays + ((size_t)prog.n_eval * sizeof(float) + 15) / 16 * 16;
+}
+
+// --------------------------------------------------------- detect workspace
+
+struct DetLayout {
+    size_t inv_off, mu_off, flags_off, total;
+};
+
+DetLayout det_layout(int64_t entries, int n_eval) {
+    DetLayout l;
+    l.inv_off = 0;
+    l.mu_off = align_up((size_t)entries * n_eval * sizeof(float));
+    l.flags_off = l.mu_off + align_up((size_t)entries * sizeof(float2));
+    l.total = l.flags_off + align_up((size_t)entries * sizeof(int32_t));
+    return l;
+}
+
+spd_status check_ws(const void *ws, size_t have, size_t need) {
+    if (need == 0) return SPD_OK;
+    if (!ws) return SPD_ERR_NO_MEMORY;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return SPD_ERR_INVALID_ARG;
+    if (have < need) return SPD_ERR_NO_MEMORY;
+    return SPD_OK;
+}
+
+spd_status check_params(const spd_search_params *q) {
+    if (!q) return SPD_ERR_INVALID_ARG;
+    if (!isfinite(q->threshold)) return SPD_ERR_INVALID_ARG;
+    if (q->sigma_mode < SPD_SIGMA_SQRTN || q->sigma_mode > SPD_SIGMA_LINEAR_EXCESS)
+        return SPD_ERR_INVALID_ARG;
+    if (!scope_ok(q->msd_scope)) return SPD_ERR_INVALID_ARG;
+    if (q->nmax_sigma < 0 || q->nmax_sigma == 1 || q->nmax_sigma > SPD_MAX_WIDTH)
+        return SPD_ERR_INVALID_ARG;
+    return SPD_OK;
+}
+
+int nmax_of(const spd_search_params *q) {
+    if (q->sigma_mode == SPD_SIGMA_SQRTN) return 0;
+    if (q->nmax_sigma) return q->nmax_sigma;
+    return q->widths && q->n_widths > 0 ? q->widths[q->n_widths - 1] : 0;
+}
+
+// Constants + one detect launch (plane output or candidates).
+spd_status run_detect(const spd_plane *p, const Program &prog, const spd_msd_stats *msd_dev,
+                      int scope, int sigma_mode, float thr, spd_candidate *out, int64_t cap,
+                      spd_result *result, float *snr_out, uint16_t *width_out,
+                      int64_t out_stride, void *ws, cudaStream_t st) {
+    const int64_t entries = entries_of(p, scope);
+    const DetLayout L = det_layout(entries, prog.n_eval);
+    char *base = static_cast<char *>(ws);
+    float *inv = reinterpret_cast<float *>(base + L.inv_off);
+    float2 *mu = reinterpret_cast<float2 *>(base + L.mu_off);
+    int32_t *flags = reinterpret_cast<int32_t *>(base + L.flags_off);
+
+    ConstArgs c;
+    c.msd = msd_dev;
+    c.entries = (int)entries;
+    c.sigma_mode = sigma_mode;
+    c.inv_tab = inv;
+    c.mu_tab = mu;
+    c.flags = flags;
+    c.result = result;
+    SPD_CK(launch_consts(c, prog, st));
+
+    DetectArgs a;
+    memset(&a, 0, sizeof(a));
+    a.data = p->data;
+    a.n_dm = p->n_dm;
+    a.n_samp = p->n_samp;
+    a.stride = p->row_stride;
+    a.scale = p->row_scale;
+    a.offset = p->row_offset;
+    a.vec_ok = plane_vec_ok(p);
+    a.per_row = scope == SPD_MSD_PER_ROW;
+    a.inv_tab = inv;
+    a.mu_tab = mu;
+    a.flags = flags;
+    a.R = program_R(prog);
+    a.tiles_per_row = (p->n_samp + kTile - 1) / kTile;
+    a.threshold = thr;
+    a.out = out;
+    a.capacity = cap;
+    a.result = result;
+    a.snr_out = snr_out;
+    a.width_out = width_out;
+    a.out_stride = out_stride;
+    SPD_CK(launch_detect(a, prog, p->dtype, snr_out != nullptr, program_smem(prog), st));
+    return SPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t spd_version(void) { return SPD_VERSION; }
+
+const char *spd_status_string(int32_t s) {
+    switch (s) {
+        case SPD_OK: return "ok";
+        case SPD_ERR_INVALID_ARG: return "invalid argument";
+        case SPD_ERR_CUDA: return "CUDA error";
+        case SPD_ERR_NO_MEMORY: return "workspace too small";
+        case SPD_ERR_OVERFLOW: return "more candidates than capacity";
+        case SPD_ERR_DEGENERATE_SIGMA: return "degenerate standard deviation";
+        case SPD_ERR_TIMEOUT: return "device wait timed out";
+        case SPD_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+int32_t spd_last_cuda_error(void) { return g_last_cuda_error; }
+
+size_t spd_msd_workspace_bytes(const spd_plane *plane, int32_t scope, int32_t nmax_sigma) {
+    (void)nmax_sigma;
+    if (check_plane(plane) != SPD_OK || !scope_ok(scope)) return 0;
+    return msd_layout(plane).total;
+}
+
+spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
+                   spd_msd_stats *out_dev, void *workspace, size_t workspace_bytes, void *stream) {
+    SPD_TRY(check_plane(plane));
+    if (!scope_ok(scope) || !out_dev) return SPD_ERR_INVALID_ARG;
+    if (nmax_sigma < 0 || nmax_sigma == 1 || nmax_sigma > SPD_MAX_WIDTH)
+        return SPD_ERR_INVALID_ARG;
+    if (nmax_sigma >= 2) return SPD_ERR_UNSUPPORTED;
+    const MsdLayout L = msd_layout(plane);
+    SPD_TRY(check_ws(workspace, workspace_bytes, L.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    MsdPart *parts = reinterpret_cast<MsdPart *>(base + L.parts_off);
+    MsdPart *scratch = reinterpret_cast<MsdPart *>(base + L.scratch_off);
+    if (!plane_empty(plane)) {
+        MsdArgs a;
+        a.data = plane->data;
+        a.n_dm = plane->n_dm;
+        a.n_samp = plane->n_samp;
+        a.stride = plane->row_stride;
+        a.scale = plane->row_scale;
+        a.offset = plane->row_offset;
+        a.units_per_row = L.upr;
+        a.vec_ok = plane_vec_ok(plane);
+        a.parts = parts;
+        SPD_CK(launch_msd_partial(a, plane->dtype, st));
+    }
+    if (scope == SPD_MSD_PER_ROW && plane->n_dm == 0) return SPD_OK;
+    SPD_CK(launch_msd_merge(parts, plane->n_dm, L.upr, plane->n_samp,
+                            scope == SPD_MSD_PER_ROW, scratch, kMergeScratch, out_dev, st));
+    return SPD_OK;
+}
+
+size_t spd_boxcar_snr_workspace_bytes(const spd_plane *plane, int32_t scope,
+                                      const int32_t *widths, int32_t n_widths) {
+    if (check_plane(plane) != SPD_OK || !scope_ok(scope)) return 0;
+    Program prog;
+    if (compile_program(widths, n_widths, prog) != SPD_OK) return 0;
+    return det_layout(entries_of(plane, scope), prog.n_eval).total;
+}
+
+spd_status spd_boxcar_snr(const spd_plane *plane, const spd_msd_stats *msd_dev, int32_t scope,
+                          const int32_t *widths, int32_t n_widths, int32_t sigma_mode,
+                          float *snr_out, uint16_t *width_out, int64_t out_stride,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    SPD_TRY(check_plane(plane));
+    if (!scope_ok(scope)) return SPD_ERR_INVALID_ARG;
+    if (sigma_mode < SPD_SIGMA_SQRTN || sigma_mode > SPD_SIGMA_LINEAR_EXCESS)
+        return SPD_ERR_INVALID_ARG;
+    static thread_local Program prog;
+    SPD_TRY(compile_program(widths, n_widths, prog));
+    if (plane_empty(plane)) return SPD_OK;
+    if (!msd_dev || !snr_out || !width_out || out_stride < plane->n_samp)
+        return SPD_ERR_INVALID_ARG;
+    const size_t need = det_layout(entries_of(plane, scope), prog.n_eval).total;
+    SPD_TRY(check_ws(workspace, workspace_bytes, need));
+    return run_detect(plane, prog, msd_dev, scope, sigma_mode, 0.f, nullptr, 0, nullptr,
+                      snr_out, width_out, out_stride, workspace,
+                      static_cast<cudaStream_t>(stream));
+}
+
+spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int64_t n_dm,
+                                    int64_t n_samp, int64_t stride, float threshold,
+                                    spd_candidate *out, int64_t capacity,
+                                    spd_result *result_dev, void *stream) {
+    if (n_dm < 0 || n_samp < 0 || n_dm > INT32_MAX || n_samp > INT32_MAX)
+        return SPD_ERR_INVALID_ARG;
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out) || !isfinite(threshold))
+        return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    const bool empty = n_dm == 0 || n_samp == 0;
+    if (!empty && (!snr || !width || stride < n_samp)) return SPD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    if (empty) return SPD_OK;
+    SPD_CK(launch_threshold(snr, width, n_dm, n_samp, stride, threshold, out, capacity,
+                            result_dev, st));
+    return SPD_OK;
+}
+
+size_t spd_detect_workspace_bytes(const spd_plane *plane, const spd_search_params *params) {
+    if (check_plane(plane) != SPD_OK || check_params(params) != SPD_OK) return 0;
+    Program prog;
+    if (compile_program(params->widths, params->n_widths, prog) != SPD_OK) return 0;
+    return det_layout(entries_of(plane, params->msd_scope), prog.n_eval).total;
+}
+
+spd_status spd_detect(const spd_plane *plane, const spd_search_params *params,
+                      const spd_msd_stats *msd_dev, spd_candidate *out, int64_t capacity,
+                      spd_result *result_dev, void *workspace, size_t workspace_bytes,
+                      void *stream) {
+    SPD_TRY(check_plane(plane));
+    SPD_TRY(check_params(params));
+    static thread_local Program prog;
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plane_empty(plane)) {
+        SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+        return SPD_OK;
+    }
+    if (!msd_dev) return SPD_ERR_INVALID_ARG;
+    const size_t need = det_layout(entries_of(plane, params->msd_scope), prog.n_eval).total;
+    SPD_TRY(check_ws(workspace, workspace_bytes, need));
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    return run_detect(plane, prog, msd_dev, params->msd_scope, params->sigma_mode,
+                      params->threshold, out, capacity, result_dev, nullptr, nullptr, 0,
+                      workspace, st);
+}
+
+size_t spd_search_workspace_bytes(const spd_plane *plane, const spd_search_params *params) {
+    if (check_plane(plane) != SPD_OK || check_params(params) != SPD_OK) return 0;
+    Program prog;
+    if (compile_program(params->widths, params->n_widths, prog) != SPD_OK) return 0;
+    const int64_t entries = entries_of(plane, params->msd_scope);
+    return msd_layout(plane).total + align_up((size_t)entries * sizeof(spd_msd_stats)) +
+           det_layout(entries, prog.n_eval).total;
+}
+
+spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
+                      spd_candidate *out, int64_t capacity, spd_result *result_dev,
+                      spd_msd_stats *msd_out_dev, void *workspace, size_t workspace_bytes,
+                      void *stream) {
+    SPD_TRY(check_plane(plane));
+    SPD_TRY(check_params(params));
+    static thread_local Program prog;
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (plane_empty(plane)) {
+        SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+        return SPD_OK;
+    }
+    const int64_t entries = entries_of(plane, params->msd_scope);
+    const MsdLayout ML = msd_layout(plane);
+    const size_t msd_bytes = align_up((size_t)entries * sizeof(spd_msd_stats));
+    const size_t need = ML.total + msd_bytes + det_layout(entries, prog.n_eval).total;
+    SPD_TRY(check_ws(workspace, workspace_bytes, need));
+    char *base = static_cast<char *>(workspace);
+    spd_msd_stats *msd = msd_out_dev ? msd_out_dev : reinterpret_cast<spd_msd_stats *>(base + ML.total);
+    SPD_TRY(spd_msd(plane, params->msd_scope, nmax_of(params), msd, base, ML.total, stream));
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    return run_detect(plane, prog, msd, params->msd_scope, params->sigma_mode,
+                      params->threshold, out, capacity, result_dev, nullptr, nullptr, 0,
+                      base + ML.total + msd_bytes, st);
+}
+
+spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out, int64_t out_stride,
+                           void *stream) {
+    SPD_TRY(check_plane(plane));
+    if (w < 1 || w > SPD_MAX_WIDTH) return SPD_ERR_INVALID_ARG;
+    if (plane_empty(plane)) return SPD_OK;
+    if (!out || out_stride < plane->n_samp || plane->n_dm > 65535) return SPD_ERR_INVALID_ARG;
+    SPD_CK(launch_boxcar_sums(*plane, w, out, out_stride, static_cast<cudaStream_t>(stream)));
+    return SPD_OK;
+}
+
+}  // extern "C"

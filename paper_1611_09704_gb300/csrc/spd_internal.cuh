@@ -1,0 +1,133 @@
+// spd_internal.cuh -- device-side structures and launchers shared by the
+// translation units of libspd.  Not part of the public ABI (include/spd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "spd.h"
+
+namespace spd {
+
+// ---------------------------------------------------------------- elements
+
+// Value of a stored element as FP32: the raw value, or fmaf(scale, q, offset)
+// when a per-row scale is given (FP16 / BF16 storage, Sec. "precision form").
+template <int DT> struct Elem;
+template <> struct Elem<SPD_F32> {
+    using T = float;
+    static __device__ __forceinline__ float cvt(T v) { return v; }
+};
+template <> struct Elem<SPD_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float cvt(T v) { return __half2float(v); }
+};
+template <> struct Elem<SPD_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float cvt(T v) { return __bfloat162float(v); }
+};
+
+inline size_t elem_bytes(int dt) { return dt == SPD_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------------- MSD
+
+constexpr int kMsdThreads = 256;
+constexpr int kMsdUnit = 65536;   // samples of one row per block-partial unit
+
+// (n, T, S) of a piece of the data, Sec. 2.1, written per unit in FP64, plus
+// the piece's smallest and largest value: sigma is exactly 0 iff they agree,
+// a test that does not depend on how S was rounded.
+struct MsdPart {
+    double n, T, S, lo, hi;
+};
+
+struct MsdArgs {
+    const void *data;
+    int64_t n_dm, n_samp, stride;
+    const float *scale, *offset;
+    int64_t units_per_row;
+    int vec_ok;          // 16-byte aligned rows: vector loads allowed
+    MsdPart *parts;      // [n_dm * units_per_row]
+};
+
+// ------------------------------------------------------------------ detect
+
+constexpr int kX = 16;              // consecutive samples owned by one thread
+constexpr int kThreads = 256;       // threads per CTA
+constexpr int kTile = kX * kThreads; // samples of one row searched per CTA
+
+// One run of the boxcar-growing program (host-compiled from the width list).
+// Each step adds one value to every running boxcar sum B: from the centred
+// samples y (src 0, positions off, off+1, ...) or from the G-sample window
+// sums S_G (src 1, positions off, off+G, ...).  If `eval`, every step
+// completes a listed width whose SNR is evaluated, eval index widx0 + step.
+// `end_group`: last evaluating run of a group of 64 eval indices.
+struct Run {
+    int16_t off;
+    int16_t count;
+    int16_t widx0;
+    uint16_t flags;   // bit 0: src, bit 1: eval, bit 2: end_group
+};
+constexpr uint16_t kRunSrcG = 1, kRunEval = 2, kRunEndGroup = 4;
+
+constexpr int kMaxRuns = 512;
+constexpr int kMaxEval = SPD_MAX_WIDTHS + 1;
+
+// The whole width program, passed by value as a __grid_constant__ kernel
+// parameter so that launching needs no host-to-device copy of its own.
+struct Program {
+    int32_t n_runs;
+    int32_t n_eval;     // evaluated widths: width 1 first, then the listed ones
+    int32_t wmax;
+    int32_t G;          // step of the coarse window sums, 0 if unused
+    Run runs[kMaxRuns];
+    uint16_t eval_w[kMaxEval];
+};
+
+struct DetectArgs {
+    const void *data;
+    int64_t n_dm, n_samp, stride;
+    const float *scale, *offset;
+    int vec_ok;
+    int per_row;                // MSD scope entry = row (else entry 0)
+    const float *inv_tab;       // [entries][n_eval]: 1 / sigma_w, FP32
+    const float2 *mu_tab;       // [entries]: mean split into hi + lo FP32
+    const int32_t *flags;       // [entries]: nonzero = degenerate sigma
+    int R;                      // row length of the transposed shared arrays
+    int64_t tiles_per_row;
+    float threshold;
+    spd_candidate *out;
+    int64_t capacity;
+    spd_result *result;
+    float *snr_out;
+    uint16_t *width_out;
+    int64_t out_stride;
+};
+
+struct ConstArgs {
+    const spd_msd_stats *msd;   // [entries]
+    int entries;
+    int sigma_mode;
+    float *inv_tab;
+    float2 *mu_tab;
+    int32_t *flags;
+    spd_result *result;   // may be null: zeroed count/status when given
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_msd_partial(const MsdArgs &a, int dtype, cudaStream_t s);
+cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t units_per_row,
+                             int64_t n_samp, int per_row, MsdPart *scratch, int n_scratch,
+                             spd_msd_stats *out, cudaStream_t s);
+cudaError_t launch_consts(const ConstArgs &a, const Program &prog, cudaStream_t s);
+cudaError_t launch_detect(const DetectArgs &a, const Program &prog, int dtype, bool plane_out,
+                          size_t smem, cudaStream_t s);
+cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,
+                             int64_t n_samp, int64_t stride, float thr, spd_candidate *out,
+                             int64_t capacity, spd_result *result, cudaStream_t s);
+cudaError_t launch_boxcar_sums(const spd_plane &p, int w, float *out, int64_t out_stride,
+                               cudaStream_t s);
+
+}  // namespace spd

@@ -1,0 +1,105 @@
+"""The C ABI library (CPU-only checks): it builds for sm_103a, loads, exports
+every function include/spd.h declares, and rejects bad arguments on the host
+before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1611_09704_gb300 as spd
+    spd.build()
+    return spd.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "spd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spd_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_calls():
+    names = _declared()
+    for must in ("spd_msd", "spd_boxcar_snr", "spd_threshold_candidates", "spd_search",
+                 "spd_detect"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1611_09704_gb300.binding import EXPORTS
+    names = _declared()
+    assert sorted(EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_sizes_match_header():
+    from paper_1611_09704_gb300 import binding as b
+    assert ctypes.sizeof(b.SpdMsdStats) == 40
+    assert ctypes.sizeof(b.SpdCandidate) == 16
+    assert ctypes.sizeof(b.SpdResult) == 16
+    assert ctypes.sizeof(b.SpdPlane) == 56
+    assert b.MSD_DTYPE.itemsize == 40 and b.CAND_DTYPE.itemsize == 16
+
+
+def _plane(n_dm=4, n_samp=100, stride=None, data=4096, dtype=0):
+    from paper_1611_09704_gb300.binding import SpdPlane
+    return SpdPlane(data, dtype, 0, n_dm, n_samp, stride or n_samp, None, None)
+
+
+def _params(widths, thr=6.0, mode=0, scope=0, nmax=0):
+    from paper_1611_09704_gb300.binding import SpdSearchParams
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    return SpdSearchParams(w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), w.size,
+                           float(thr), mode, scope, nmax, 0), w
+
+
+def test_host_validation(lib):
+    from paper_1611_09704_gb300.binding import SPD_ERR_INVALID_ARG
+    p = _plane()
+    ws = lib.spd_msd_workspace_bytes(ctypes.byref(p), 0, 0)
+    assert ws > 0
+    assert lib.spd_msd_workspace_bytes(ctypes.byref(_plane(stride=50)), 0, 0) == 0
+    assert lib.spd_msd_workspace_bytes(ctypes.byref(p), 7, 0) == 0
+    prm, keep = _params(np.arange(1, 33))
+    assert lib.spd_search_workspace_bytes(ctypes.byref(p), ctypes.byref(prm)) > ws
+    # width lists: not ascending, zero, too wide -> no workspace size
+    for bad in ([3, 2], [0, 1], [1, 5000], [4, 4]):
+        q, k = _params(bad)
+        assert lib.spd_search_workspace_bytes(ctypes.byref(p), ctypes.byref(q)) == 0
+    q, k = _params([1, 2], thr=float("nan"))
+    assert lib.spd_search_workspace_bytes(ctypes.byref(p), ctypes.byref(q)) == 0
+    # calls fail before any launch
+    assert lib.spd_search(ctypes.byref(p), ctypes.byref(prm), None, 0, None, None, None, 0,
+                          None) == SPD_ERR_INVALID_ARG
+    assert lib.spd_search(None, ctypes.byref(prm), None, 0, None, None, None, 0,
+                          None) == SPD_ERR_INVALID_ARG
+    assert lib.spd_threshold_candidates(None, None, 4, 10, 10, 6.0, None, 5, None,
+                                        None) == SPD_ERR_INVALID_ARG
+    assert lib.spd_boxcar_sums(ctypes.byref(p), 0, None, 100, None) == SPD_ERR_INVALID_ARG
+    # misaligned data pointer for f32
+    bad = _plane(data=4098)
+    assert lib.spd_msd_workspace_bytes(ctypes.byref(bad), 0, 0) == 0
+
+
+def test_workspace_grows_with_scope_and_widths(lib):
+    p = _plane(n_dm=64, n_samp=65536)
+    a, k1 = _params(np.arange(1, 33))
+    b, k2 = _params(np.arange(1, 33), scope=1)
+    c, k3 = _params(np.arange(1, 513))
+    wa = lib.spd_detect_workspace_bytes(ctypes.byref(p), ctypes.byref(a))
+    wb = lib.spd_detect_workspace_bytes(ctypes.byref(p), ctypes.byref(b))
+    wc = lib.spd_detect_workspace_bytes(ctypes.byref(p), ctypes.byref(c))
+    assert 0 < wa < wb and wa < wc
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.spd_status_string(s)
+    assert lib.spd_version() >= 100

@@ -1,0 +1,206 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded
+synthetic planes: MSD (step a), per-sample best SNR and width (steps b, c),
+candidate lists (step d), the fused search, and the edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def spd():
+    import paper_1611_09704_gb300 as m
+    m.build()
+    m.load()
+    return m
+
+
+def _oracle_plane(x, n_samp, scale=None, offset=None):
+    """Host copy of a device plane as the oracle's Plane."""
+    dt = {torch.float32: "f32", torch.float16: "f16", torch.bfloat16: "bf16"}[x.dtype]
+    return oracle.Plane(synth.to_host_numpy(x), dtype=dt, n_samp=n_samp,
+                        scale=None if scale is None else scale.cpu().numpy(),
+                        offset=None if offset is None else offset.cpu().numpy())
+
+
+def _full_case(spd, x, n_samp, widths, thr, scope=0, scale=None, offset=None, capacity=None):
+    """Run every GPU call on x and compare each with the oracle."""
+    op = _oracle_plane(x, n_samp, scale, offset)
+    mean, sd, _, tab = oracle.msd_and_sigma(op, widths, oracle.SIGMA_SQRTN, scope)
+    kw = dict(n_samp=n_samp, scale=scale, offset=offset)
+
+    m = spd.msd(x, scope, **kw)
+    torch.cuda.synchronize()
+    P.check_msd(spd.msd_to_numpy(m), mean, sd)
+
+    best_o, win_o = oracle.boxcar_snr(op, mean, sd, tab, widths, scope)
+    snr_g, w_g = spd.boxcar_snr(x, m, widths, spd.SIGMA_SQRTN, scope, **kw)
+    torch.cuda.synchronize()
+
+    def sigma_of(e, w):
+        return float(np.atleast_1d(sd)[e] * math.sqrt(w))
+
+    P.check_plane(snr_g.cpu().numpy(), spd.widths_to_numpy(w_g), best_o, win_o, op, mean,
+                  sigma_of, scope=scope)
+
+    n_o = int((best_o >= thr).sum())
+    cap = capacity if capacity is not None else max(n_o + 64, 16)
+    out, res, _ = spd.search(x, widths, thr, cap, spd.SIGMA_SQRTN, scope, **kw)
+    count, status = spd.read_result(res)
+    assert status == 0
+    recs = spd.candidates_to_numpy(out, count)
+    P.check_candidates(recs, count, cap, best_o, thr, win_o=win_o, plane=op, mean=mean,
+                       sigma_of=sigma_of, scope=scope)
+
+    # the fused kernel and threshold-on-the-plane agree exactly
+    out2, res2 = spd.threshold_candidates(snr_g, w_g, thr, cap, n_samp=n_samp)
+    c2, s2 = spd.read_result(res2)
+    r2 = spd.candidates_to_numpy(out2, c2)
+    assert c2 == count
+    if count <= cap:
+        a = np.sort(recs, order=["dm", "sample"])
+        b = np.sort(r2, order=["dm", "sample"])
+        assert np.array_equal(a["dm"], b["dm"]) and np.array_equal(a["sample"], b["sample"])
+        assert np.array_equal(a["width"], b["width"]) and np.array_equal(a["snr"], b["snr"])
+    return count, best_o
+
+
+def test_plain_fp32_config(spd):
+    """64 DM x 65536 samples, N(0,1), five top-hats, widths 1..32, threshold 6."""
+    sp = synth.plain_tophat(64, 65536, device=DEV, seed=1611_0)
+    count, best_o = _full_case(spd, sp.data, sp.n_samp, list(range(1, 33)), 6.0)
+    for p in sp.pulses:
+        assert best_o[p.dm, p.sample] >= 6.0
+
+
+@pytest.mark.parametrize("n_dm,n_samp,stride", [(5, 10001, 10016), (3, 4097, 4097),
+                                                (2, 4095, 4100), (7, 13, 16), (3, 1, 1),
+                                                (1, 8191, 8192)])
+def test_ragged_shapes(spd, n_dm, n_samp, stride):
+    sp = synth.plain_tophat(n_dm, n_samp, widths=(3,) if n_samp > 200 else (), device=DEV,
+                            seed=n_samp, stride=stride)
+    _full_case(spd, sp.data, n_samp, list(range(1, 33)), 3.0)
+
+
+@pytest.mark.parametrize("widths", [
+    [1], [7], [2, 3, 5, 9, 17, 40, 100], list(range(1, 17)) + list(range(24, 257, 8)),
+    [1, 2, 4, 8, 16, 32, 64, 128], list(range(4, 200, 4)), [16, 32, 48, 64, 80],
+    list(range(1, 301)), [1, 64, 1024, 4096], list(range(100, 165))])
+def test_width_programs(spd, widths):
+    """Width lists exercising fine steps, coarse steps of 4/8/16, irregular gaps,
+    more than 64 widths (several groups) and the widest halo."""
+    sp = synth.ska_like(4, 12000, n_pulses=6, device=DEV, seed=len(widths) + widths[-1],
+                        drift_period=4096)
+    _full_case(spd, sp.data, sp.n_samp, widths, 7.0)
+
+
+def test_ska_like_small(spd):
+    """The SKA-like recipe (drift + Gaussian pulses) at reduced size, config widths."""
+    widths = list(range(1, 17)) + list(range(24, 257, 8))
+    sp = synth.ska_like(16, 65536 + 333, n_pulses=20, device=DEV, seed=1611_1)
+    count, _ = _full_case(spd, sp.data, sp.n_samp, widths, 7.0)
+    assert count > 0
+
+
+def test_per_row_scope(spd):
+    sp = synth.ska_like(6, 20000, n_pulses=4, device=DEV, seed=9)
+    _full_case(spd, sp.data, sp.n_samp, list(range(1, 65)), 6.0, scope=1)
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_half_storage_with_scale_offset(spd, dt):
+    sp = synth.ska_like(6, 30000, n_pulses=5, device=DEV, seed=21)
+    q = synth.quantise_rows(sp, dt)
+    off = torch.linspace(-3, 3, q.n_dm, device=DEV, dtype=torch.float32)
+    _full_case(spd, q.data, q.n_samp, list(range(1, 17)) + list(range(24, 129, 8)), 7.0,
+               scale=q.scale, offset=off)
+    _full_case(spd, q.data, q.n_samp, list(range(1, 33)), 7.0, scale=q.scale)
+
+
+def test_integer_ties(spd):
+    """Small integer data gives exact SNR ties between widths; any tied width
+    passes, the SNR must match."""
+    g = torch.Generator(device=DEV).manual_seed(4)
+    x = torch.randint(-2, 3, (4, 3000), generator=g, device=DEV).to(torch.float32)
+    _full_case(spd, x, 3000, list(range(1, 9)), 2.5)
+
+
+def test_overflow_keeps_exact_count(spd):
+    sp = synth.ska_like(4, 30000, n_pulses=2, device=DEV, seed=5, drift_period=8192)
+    count, _ = _full_case(spd, sp.data, sp.n_samp, list(range(1, 65)), 3.0, capacity=100)
+    assert count > 100
+
+
+def test_degenerate_sigma(spd):
+    x = torch.full((3, 5000), 2.5, device=DEV)
+    m = spd.msd(x)
+    out, res, msd = spd.search(x, [1, 2, 4], 6.0, 10)
+    count, status = spd.read_result(res)
+    assert count == 0 and status == 5
+    assert spd.msd_to_numpy(msd)["status"][0] == 5
+    assert spd.msd_to_numpy(m)["status"][0] == 5
+    snr, w = spd.boxcar_snr(x, m, [1, 2, 4])
+    assert torch.isnan(snr).all() and (w == 0).all()
+
+
+def test_empty_planes(spd):
+    for shape in [(0, 100), (4, 0)]:
+        x = torch.empty(shape, device=DEV)
+        out, res, _ = spd.search(x, [1, 2], 6.0, 4)
+        assert spd.read_result(res) == (0, 0)
+
+
+def test_repeat_calls_are_deterministic(spd):
+    sp = synth.ska_like(8, 40000, n_pulses=10, device=DEV, seed=77)
+    w = list(range(1, 17)) + list(range(24, 257, 8))
+    o1, r1, m1 = spd.search(sp.data, w, 7.0, 200000)
+    o2, r2, m2 = spd.search(sp.data, w, 7.0, 200000)
+    c1, c2 = spd.read_result(r1)[0], spd.read_result(r2)[0]
+    assert c1 == c2
+    assert torch.equal(m1, m2)
+    a = np.sort(spd.candidates_to_numpy(o1, c1), order=["dm", "sample"])
+    b = np.sort(spd.candidates_to_numpy(o2, c2), order=["dm", "sample"])
+    assert np.array_equal(a, b)
+
+
+def test_boxcar_sums_closed_forms(spd):
+    n = 3000
+    c = torch.full((2, n), 3.0, device=DEV)
+    for w in (1, 7, 64, 999):
+        s = spd.boxcar_sums(c, w).cpu().numpy()
+        assert np.array_equal(s[:, : n - w + 1], np.full((2, n - w + 1), 3.0 * w))
+        assert np.isnan(s[:, n - w + 1:]).all()
+    ramp = (5.0 + 2.0 * torch.arange(n, device=DEV, dtype=torch.float32)).reshape(1, -1)
+    for w in (1, 3, 50):
+        i = np.arange(n - w + 1)
+        want = w * 5.0 + 2.0 * (w * i + w * (w - 1) / 2)
+        assert np.array_equal(spd.boxcar_sums(ramp, w).cpu().numpy()[0, : n - w + 1], want)
+    x = torch.randn(3, 5000, device=DEV)
+    for w in (1, 5, 256):
+        g = spd.boxcar_sums(x, w).cpu().numpy()
+        o = oracle.boxcar_sums(x.cpu().numpy(), w)
+        ok = np.isfinite(o)
+        assert np.array_equal(np.isnan(g), ~ok)
+        assert np.allclose(g[ok], o[ok], rtol=1e-5, atol=1e-5 * math.sqrt(w))
+
+
+def test_figure1_tophat_response(spd):
+    """A top-hat of width W on zero-mean unit noise is found at its leading
+    sample with width W (Figure 1)."""
+    for W in (1, 4, 13, 32):
+        x = torch.zeros((1, 4096), device=DEV)
+        x[0, ::2] = 1.0
+        x[0, 1::2] = -1.0      # mean 0, sd 1
+        x[0, 1000:1000 + W] += 25.0 / math.sqrt(W)
+        m = spd.msd(x)
+        snr, w = spd.boxcar_snr(x, m, list(range(1, 65)))
+        assert int(spd.widths_to_numpy(w)[0, 1000]) in (W, W + 1, W - 1 if W > 1 else 1)

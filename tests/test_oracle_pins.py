@@ -352,3 +352,13 @@ def test_search_finds_injected_tophats():
         top = sel[np.argmax(sel["snr"])]
         assert abs(top["snr"] - p.snr) < 4.0
         assert abs(int(top["width"]) - p.width) <= max(2, p.width // 3)
+
+
+def test_snr_at_matches_closed_form():
+    """One-pair SNR: a ramp's window sum is closed-form; past the row end NaN."""
+    n, a, b = 50, 2.0, 0.5
+    ramp = (a + b * np.arange(n)).astype(np.float32).reshape(1, -1)
+    i, w, mu, sw = 7, 9, 1.25, 3.0
+    want = (w * a + b * (w * i + w * (w - 1) / 2) - w * mu) / sw
+    assert oracle.snr_at(ramp, 0, i, w, mu, sw) == pytest.approx(want, rel=1e-15)
+    assert math.isnan(oracle.snr_at(ramp, 0, 45, 9, mu, sw))
