@@ -160,6 +160,29 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
                    spd_msd_stats *out_dev, void *workspace, size_t workspace_bytes,
                    void *stream);
 
+/* The same MSD as spd_msd, for callers that cannot give the library a
+ * workspace.  The paper has no counterpart: this is a deployment aid.
+ * Some callers must not allocate device memory once they run -- a real-time
+ * backend that fixes its memory at start-up because a later cudaMalloc can
+ * stall the device, or a plain C caller that holds only its plane and output
+ * and has no allocator to size a workspace with.  They pass the plane and
+ * out_dev (1 or n_dm spd_msd_stats, device) as for spd_msd, and the block
+ * partials go to a static array of 1,320,960 bytes that the library declares
+ * in device memory; every GPU that loads the library keeps it until the
+ * process exits.  Limit: n_dm * ceil(n_samp / SPD_MSD_UNIT_SAMPLES) must not
+ * exceed SPD_MSD_NOALLOC_MAX_UNITS (e.g. 4096 x 524288), else the call returns
+ * SPD_ERR_NO_MEMORY and launches nothing.  The first call on each device looks
+ * up the array's device address (a CUDA runtime query); make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race and give wrong results; calls ordered on one stream do not.  Nothing in
+ * the array needs clearing between calls -- each call writes every entry it
+ * reads.  Errors: as spd_msd. */
+#define SPD_MSD_UNIT_SAMPLES 65536
+#define SPD_MSD_NOALLOC_MAX_UNITS 32768
+spd_status spd_msd_noalloc(const spd_plane *plane, int32_t scope, spd_msd_stats *out_dev,
+                           void *stream);
+
 /* Bytes of device workspace spd_boxcar_snr needs. */
 size_t spd_boxcar_snr_workspace_bytes(const spd_plane *plane, int32_t scope,
                                       const int32_t *widths, int32_t n_widths);

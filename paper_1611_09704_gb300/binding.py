@@ -69,7 +69,8 @@ CAND_DTYPE = np.dtype([("dm", "<i4"), ("sample", "<i4"), ("snr", "<f4"), ("width
 EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_workspace_bytes", "spd_msd", "spd_boxcar_snr_workspace_bytes",
            "spd_boxcar_snr", "spd_threshold_candidates", "spd_detect_workspace_bytes",
-           "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums"]
+           "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums",
+           "spd_msd_noalloc"]
 
 
 class SpdError(RuntimeError):

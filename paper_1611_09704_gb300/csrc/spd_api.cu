@@ -262,6 +262,11 @@ spd_status run_detect(const spd_plane *p, const Program &prog, const spd_msd_sta
 
 }  // namespace
 
+namespace spd {
+// Records a CUDA error for spd_last_cuda_error from other translation units.
+void note_cuda_error(int e) { g_last_cuda_error = e; }
+}  // namespace spd
+
 extern "C" {
 
 int32_t spd_version(void) { return SPD_VERSION; }
