@@ -82,10 +82,12 @@ MsdLayout msd_layout(const spd_plane *p) {
 // ----------------------------------------------------------- width program
 
 // Evaluated widths are width 1 (the starting value of Algorithm 1) followed
-// by the listed widths.  Between consecutive evaluated widths the running sum
-// grows by d samples: q steps of a G-sample window sum and r single samples
-// (d = qG + r), the last step completing the width.  Steps are grouped into
-// runs of one kind.  G is chosen to minimise the number of steps.
+// by the listed widths.  They are cut into groups of consecutive widths that
+// step by 1 (the running sum adds one sample per width) or by G (it adds one
+// G-sample window sum); a group's sums start from the prefix sums at `off`.
+// Groups hold at most 16 (step 1) or 2 (16/G + 1) (step G) widths, doubled
+// until there are at most 64 groups, and never cross a multiple of 64 in eval
+// index.  G is the most frequent step of 8 or 16, if any.
 spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
     if (!widths || n < 1 || n > SPD_MAX_WIDTHS) return SPD_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k) {
@@ -97,79 +99,69 @@ spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
     for (int k = 0; k < n; ++k) E.push_back(widths[k]);
     const int ne = (int)E.size();
 
-    auto cost = [&](int g) {
-        long c = 0;
-        for (int k = 1; k < ne; ++k) {
-            const int d = E[k] - E[k - 1];
-            c += g ? d / g + d % g : d;
-        }
-        return c + (g ? 4 : 0);   // building S_G costs about a few steps per sample
-    };
-    int G = 0;
-    long best = cost(0);
-    for (int g : {4, 8, 16}) {
-        const long c = cost(g);
-        if (c < best) { best = c; G = g; }
-    }
-
-    struct Step { int src, pos, eval, widx; };
-    std::vector<Step> steps;
-    steps.push_back({0, 0, 1, 0});
-    int pos = 1;
+    int n8 = 0, n16 = 0;
     for (int k = 1; k < ne; ++k) {
-        const int d = E[k] - E[k - 1];
-        const int q = G ? d / G : 0;
-        const int r = G ? d % G : d;
-        for (int j = 0; j < q; ++j) { steps.push_back({1, pos, 0, -1}); pos += G; }
-        for (int j = 0; j < r; ++j) { steps.push_back({0, pos, 0, -1}); pos += 1; }
-        steps.back().eval = 1;
-        steps.back().widx = k;
+        n8 += E[k] - E[k - 1] == 8;
+        n16 += E[k] - E[k - 1] == 16;
     }
+    const int G = (n8 || n16) ? (n8 >= n16 ? 8 : 16) : 0;
 
-    std::vector<Run> runs;
-    std::vector<int> rstride;
-    for (const Step &s : steps) {
-        const int stride = s.src ? G : 1;
-        if (!runs.empty()) {
-            Run &b = runs.back();
-            const int bsrc = (b.flags & kRunSrcG) ? 1 : 0;
-            const int beval = (b.flags & kRunEval) ? 1 : 0;
-            const bool same = bsrc == s.src && beval == s.eval &&
-                              b.off + b.count * rstride.back() == s.pos && b.count < 32000 &&
-                              (!s.eval || ((b.widx0 >> 6) == (s.widx >> 6)));
-            if (same) { b.count++; continue; }
+    std::vector<Group> groups;
+    for (int scale = 1;; scale *= 2) {
+        const int max_fine = 16 * scale, max_coarse = (G ? 2 * (16 / G + 1) : 1) * scale;
+        groups.clear();
+        for (int k = 0; k < ne; ++k) {
+            const int step = k ? E[k] - E[k - 1] : 1;
+            if (!groups.empty()) {
+                Group &g = groups.back();
+                const bool coarse = g.flags & kGroupCoarse;
+                const bool fits = coarse ? (G && step == G && g.count < max_coarse)
+                                         : (step == 1 && g.count < max_fine);
+                if (fits && (k >> 6) == (g.widx0 >> 6)) {
+                    g.count++;
+                    continue;
+                }
+            }
+            Group g;
+            const bool coarse = G && step == G;
+            g.off = (int16_t)(E[k] - (coarse ? G : 1));
+            g.count = 1;
+            g.widx0 = (int16_t)k;
+            g.flags = coarse ? kGroupCoarse : 0;
+            groups.push_back(g);
         }
-        Run r;
-        r.off = (int16_t)s.pos;
-        r.count = 1;
-        r.widx0 = (int16_t)(s.eval ? s.widx : 0);
-        r.flags = (uint16_t)((s.src ? kRunSrcG : 0) | (s.eval ? kRunEval : 0));
-        runs.push_back(r);
-        rstride.push_back(stride);
+        if ((int)groups.size() <= kMaxCodeGroups) break;
+        if (max_fine > SPD_MAX_WIDTHS) return SPD_ERR_UNSUPPORTED;   // irregular lists
     }
-    for (Run &r : runs) {
-        if (!(r.flags & kRunEval)) continue;
-        const int last = r.widx0 + r.count - 1;
-        if ((last & 63) == 63 || last == ne - 1) r.flags |= kRunEndGroup;
-    }
-    if ((int)runs.size() > kMaxRuns) return SPD_ERR_UNSUPPORTED;
 
     memset(&prog, 0, sizeof(prog));
-    prog.n_runs = (int)runs.size();
+    prog.n_groups = (int)groups.size();
     prog.n_eval = ne;
     prog.wmax = E.back();
     prog.G = G;
-    for (size_t i = 0; i < runs.size(); ++i) prog.runs[i] = runs[i];
+    for (size_t i = 0; i < groups.size(); ++i) prog.groups[i] = groups[i];
     for (int k = 0; k < ne; ++k) prog.eval_w[k] = (uint16_t)E[k];
     return SPD_OK;
 }
 
+// Blocks of 16 positions staged per tile: the tile, the halo and slack for
+// window loads that run past the last width.
 int program_R(const Program &prog) { return (kTile + prog.wmax + 32 + 15) / 16 + 1; }
+int program_span(const Program &prog) { return kTile + prog.wmax - 1; }
+int program_raw_bytes(const Program &prog, int dtype) {
+    return (int)((program_span(prog) * elem_bytes(dtype) + 15) / 16 * 16);
+}
 
-size_t program_smem(const Program &prog) {
-    const int R = program_R(prog);
-    const size_t arrays = (size_t)(prog.G ? 2 : 1) * kX * R * sizeof(float);
-    return arrays + ((size_t)prog.n_eval * sizeof(float) + 15) / 16 * 16;
+// Shared memory of one detect CTA: two raw staging buffers, the centred
+// samples and window sums (20 words per 16 positions), per-block prefix data,
+// 1/sigma_w per width and per group.
+size_t program_smem(const Program &prog, int dtype) {
+    const size_t R = program_R(prog);
+    size_t b = 16 + 2 * (size_t)program_raw_bytes(prog, dtype);
+    b += (size_t)(prog.G ? 2 : 1) * 20 * R * sizeof(float);
+    b += R * 3 * sizeof(float);   // block sums, largest and smallest prefix
+    b += ((size_t)prog.n_eval + prog.n_groups) * sizeof(float);
+    return (b + 15) / 16 * 16;
 }
 
 // --------------------------------------------------------- detect workspace
@@ -248,6 +240,8 @@ spd_status run_detect(const spd_plane *p, const Program &prog, const spd_msd_sta
     a.mu_tab = mu;
     a.flags = flags;
     a.R = program_R(prog);
+    a.span = program_span(prog);
+    a.raw_bytes = program_raw_bytes(prog, p->dtype);
     a.tiles_per_row = (p->n_samp + kTile - 1) / kTile;
     a.threshold = thr;
     a.out = out;
@@ -256,7 +250,7 @@ spd_status run_detect(const spd_plane *p, const Program &prog, const spd_msd_sta
     a.snr_out = snr_out;
     a.width_out = width_out;
     a.out_stride = out_stride;
-    SPD_CK(launch_detect(a, prog, p->dtype, snr_out != nullptr, program_smem(prog), st));
+    SPD_CK(launch_detect(a, prog, p->dtype, snr_out != nullptr, program_smem(prog, p->dtype), st));
     return SPD_OK;
 }
 

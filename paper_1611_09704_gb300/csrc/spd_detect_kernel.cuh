@@ -1,26 +1,43 @@
-// spd_detect_kernel.cuh -- steps (b), (c), (d): boxcar filters, SNR, max over widths
-// with the winning width, and thresholding with compaction (Sec. 2.3-2.4,
-// Algorithm 1), in one kernel per DM-row tile.
+// spd_detect_kernel.cuh -- steps (b), (c), (d): boxcar filters, SNR, max over
+// widths with the winning width, and thresholding with compaction (Sec. 2.3-2.4,
+// Algorithm 1).
 //
-// A CTA of 256 threads owns kTile = 4096 consecutive samples of one DM row and
-// stages them, plus the (wmax - 1)-sample halo to their right, once in shared
-// memory as centred values y = x - mu.  Each thread owns kX = 16 consecutive
-// start samples and keeps their running boxcar sums B[k] in registers; the
-// sums grow one step at a time as in Algorithm 1 (B = B + x[...]) from either
-// a single sample y or a precomputed G-sample window sum S_G (for width lists
-// that step by G), so B_w carries no large-prefix cancellation.  For every
-// listed width: SNR = B * (1/sigma_w) and a running max.
+// Persistent CTAs of 256 threads walk the plane's tiles (kTile = 4096
+// consecutive samples of one DM row).  Each tile's window -- the tile plus the
+// (wmax - 1)-sample halo to its right -- arrives in shared memory by a 1-D
+// bulk (TMA) copy issued one tile ahead, so the copy of tile k+1 overlaps the
+// arithmetic of tile k.  The window is then staged as centred values
+// y = x - mu, G-sample window sums S_G, and per 16-position block a
+// compensated (hi + lo) prefix sum of y with the block's largest and smallest
+// prefix value.
 //
-// The winning width travels with the max: the low 6 mantissa bits of each SNR
-// are replaced by a code (63 - index within a group of 64 widths) before a
-// plain float max, so one max instruction keeps both, and among SNRs equal to
+// Each thread owns kX = 16 consecutive start samples and keeps their running
+// boxcar sums B in registers as eight pairs of adjacent samples (one packed
+// f32x2 add or multiply serves two samples).  Widths are taken in groups: a
+// group's sums start from the prefix sums (B_off = C[i+off] - C[i]) and grow
+// one step per width as in Algorithm 1 (B = B + x[...]); SNR = B * (1/sigma_w).
+//
+// Plane output (every sample's best SNR and width): the low 6 mantissa bits of
+// each SNR are replaced by a code (63 - index within a block of 64 widths)
+// before a float max, so one max keeps value and width; among SNRs equal to
 // 2^-17 relative the smallest width wins -- the strict ">" of Algorithm 1 at
-// that resolution.  Widths past the row end see y = -inf, which packs to NaN
-// and is ignored by max.
+// that resolution.
 //
-// Shared arrays are stored transposed ([16][R], position p at
-// (p % 16) * R + p / 16) so that the 32 lanes of a warp, each reading
-// "its own start + the same offset", hit 32 consecutive words.
+// Candidate search: per group only the value max is kept (three-input max,
+// two widths per instruction); the group's index is packed into it instead.
+// Before a group is evaluated, an upper bound of its SNRs over the thread's 16
+// samples -- (max prefix over the positions it reaches - min prefix at the
+// samples) * max 1/sigma_w -- is compared with max(threshold, the smallest
+// current best of the 16 samples); a group that cannot reach either cannot
+// change any candidate and is skipped.  Groups are visited from the widest
+// down.  For the candidates alone the winning group is evaluated again (same
+// arithmetic, so bitwise the same SNRs) to find the first width whose SNR
+// equals the kept maximum -- the same width the plane output reports.
+//
+// Widths past the row end see y = -inf (sums -inf or NaN), ignored by max.
+// Shared arrays hold 16 positions in 20 words (4 padding words per block of
+// 16): lane t reads "16 t + offset", so 32 lanes hit distinct banks and
+// 128-bit loads are conflict-free within each quarter warp.
 #pragma once
 #include "spd_internal.cuh"
 
@@ -30,8 +47,16 @@ namespace spd {
 
 namespace {
 
+constexpr int kPad = 20;             // shared words per 16 positions
+constexpr int kWaitLimit = 1 << 22;  // bounded spin on a bulk copy (seconds)
+
+__device__ __forceinline__ int padr(int p) { return (p & 15) + kPad * (p >> 4); }
+
 __device__ __forceinline__ float packw(float s, uint32_t code) {
     return __uint_as_float((__float_as_uint(s) & 0xFFFFFFC0u) | code);
+}
+__device__ __forceinline__ float trunc17(float s) {
+    return __uint_as_float(__float_as_uint(s) & 0xFFFFFFC0u);
 }
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -40,8 +65,51 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
-__device__ __forceinline__ float ld_t(const float *base_t, int R, int off) {
-    return base_t[(off & (kX - 1)) * R + (off >> 4)];
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// ------------------------------------------------------------- bulk copies
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One arrival that also expects `bytes` of bulk-copy completion.
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for a phase of `bar`; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_test(bar, phase)) return true;
+    return false;
 }
 
 template <int DT>
@@ -50,13 +118,13 @@ __device__ __forceinline__ void load4v(const typename Elem<DT>::T *p, float &a, 
 template <>
 __device__ __forceinline__ void load4v<SPD_F32>(const float *p, float &a, float &b, float &c,
                                                 float &d) {
-    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    const float4 v = *reinterpret_cast<const float4 *>(p);
     a = v.x; b = v.y; c = v.z; d = v.w;
 }
 template <>
 __device__ __forceinline__ void load4v<SPD_F16>(const __half *p, float &a, float &b, float &c,
                                                 float &d) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p));
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
     const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
     const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
     a = lo.x; b = lo.y; c = hi.x; d = hi.y;
@@ -64,349 +132,742 @@ __device__ __forceinline__ void load4v<SPD_F16>(const __half *p, float &a, float
 template <>
 __device__ __forceinline__ void load4v<SPD_BF16>(const __nv_bfloat16 *p, float &a, float &b,
                                                  float &c, float &d) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p));
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
     const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
     const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
     a = lo.x; b = lo.y; c = hi.x; d = hi.y;
 }
 
-// Running state of one thread: kX boxcar sums and kX packed maxima.
-struct State {
-    float B[kX];
-    float best[kX];
+// ------------------------------------------------------- double-float sums
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    const float lo = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    return two_sum(s.x, lo);
+}
+
+// ------------------------------------------------------------ width sinks
+
+// Candidate search: value max of the current group per sample.
+struct MaxSink {
+    float m[kX];
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int k = 0; k < kX; ++k) m[k] = -INFINITY;
+    }
+    __device__ __forceinline__ void two(int j, int, float2 sa, float2 sb) {
+        m[2 * j] = fmax3(m[2 * j], sa.x, sb.x);
+        m[2 * j + 1] = fmax3(m[2 * j + 1], sa.y, sb.y);
+    }
+    __device__ __forceinline__ void one(int j, int, float2 sa) {
+        m[2 * j] = fmaxf(m[2 * j], sa.x);
+        m[2 * j + 1] = fmaxf(m[2 * j + 1], sa.y);
+    }
 };
 
-// d = 1 run from y: widths c0 + cc use W[k + cc].
-__device__ __forceinline__ void run_fine(State &st, const float *sy_t, int R, const Run &r,
-                                         const float *s_inv) {
-    const bool eval = (r.flags & kRunEval) != 0;
-    float W[2 * kX];
+// Plane output: packed (SNR, width code) max per sample.
+struct PackSink {
+    float best[kX];
+    __device__ __forceinline__ void two(int j, int wi, float2 sa, float2 sb) {
+        const uint32_t ka = 63u - (uint32_t)(wi & 63), kb = 63u - (uint32_t)((wi + 1) & 63);
+        best[2 * j] = fmax3(best[2 * j], packw(sa.x, ka), packw(sb.x, kb));
+        best[2 * j + 1] = fmax3(best[2 * j + 1], packw(sa.y, ka), packw(sb.y, kb));
+    }
+    __device__ __forceinline__ void one(int j, int wi, float2 sa) {
+        const uint32_t ka = 63u - (uint32_t)(wi & 63);
+        best[2 * j] = fmaxf(best[2 * j], packw(sa.x, ka));
+        best[2 * j + 1] = fmaxf(best[2 * j + 1], packw(sa.y, ka));
+    }
+};
+
+// Recovery: first eval index whose SNR, packed with the group's code, equals
+// the kept maximum (truncated value | (63 - group)) -- only possible for the
+// samples whose winner lies in the group being re-evaluated.
+struct FindSink {
+    float best[kX];
+    int found[kX];
+    uint32_t code;       // 63 - group
+    __device__ __forceinline__ void test(int k, int wi, float s) {
+        if (found[k] < 0 && __float_as_uint(packw(s, code)) == __float_as_uint(best[k]))
+            found[k] = wi;
+    }
+    __device__ __forceinline__ void two(int j, int wi, float2 sa, float2 sb) {
+        test(2 * j, wi, sa.x);
+        test(2 * j + 1, wi, sa.y);
+        test(2 * j, wi + 1, sb.x);
+        test(2 * j + 1, wi + 1, sb.y);
+    }
+    __device__ __forceinline__ void one(int j, int wi, float2 sa) {
+        test(2 * j, wi, sa.x);
+        test(2 * j + 1, wi, sa.y);
+    }
+};
+
+// Two consecutive widths (eval indices wi, wi+1) with step values Va, Vb.
+template <class Sink>
+__device__ __forceinline__ void eval2(float2 *B, Sink &sk, const float2 *Va, const float2 *Vb,
+                                      int wi, const float *s_inv) {
+    const float ia = s_inv[wi], ib = s_inv[wi + 1];
+    const float2 ia2 = make_float2(ia, ia), ib2 = make_float2(ib, ib);
 #pragma unroll
-    for (int m = 0; m < kX; ++m) W[m] = ld_t(sy_t, R, r.off + m);
-    for (int c0 = 0; c0 < r.count; c0 += kX) {
-#pragma unroll
-        for (int m = 0; m < kX; ++m) W[kX + m] = ld_t(sy_t, R, r.off + c0 + kX + m);
-        if (eval) {
-#pragma unroll
-            for (int cc = 0; cc < kX; cc += 2) {
-                const int c = c0 + cc;
-                if (c + 1 < r.count) {
-                    const int wi = r.widx0 + c;
-                    const float i0 = s_inv[wi], i1 = s_inv[wi + 1];
-                    const uint32_t k0 = 63u - (uint32_t)(wi & 63);
-                    const uint32_t k1 = 63u - (uint32_t)((wi + 1) & 63);
-#pragma unroll
-                    for (int k = 0; k < kX; ++k) {
-                        st.B[k] += W[k + cc];
-                        const float s0 = st.B[k] * i0;
-                        st.B[k] += W[k + cc + 1];
-                        const float s1 = st.B[k] * i1;
-                        st.best[k] = fmax3(st.best[k], packw(s0, k0), packw(s1, k1));
-                    }
-                } else if (c < r.count) {
-                    const int wi = r.widx0 + c;
-                    const float i0 = s_inv[wi];
-                    const uint32_t k0 = 63u - (uint32_t)(wi & 63);
-#pragma unroll
-                    for (int k = 0; k < kX; ++k) {
-                        st.B[k] += W[k + cc];
-                        st.best[k] = fmaxf(st.best[k], packw(st.B[k] * i0, k0));
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int cc = 0; cc < kX; ++cc) {
-                if (c0 + cc < r.count) {
-#pragma unroll
-                    for (int k = 0; k < kX; ++k) st.B[k] += W[k + cc];
-                }
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < kX; ++m) W[m] = W[kX + m];
+    for (int j = 0; j < kX / 2; ++j) {
+        B[j] = add2(B[j], Va[j]);
+        const float2 sa = mul2(B[j], ia2);
+        B[j] = add2(B[j], Vb[j]);
+        const float2 sb = mul2(B[j], ib2);
+        sk.two(j, wi, sa, sb);
     }
 }
 
-// d = G run from S_G: width c uses S_G at offsets off + c*G + k, k < 16.
-// Segments of G values live in a ring of NS = 16/G + 1 slots.
-template <int G>
-__device__ __forceinline__ void run_coarse(State &st, const float *sg_t, int R, const Run &r,
-                                           const float *s_inv) {
-    const bool eval = (r.flags & kRunEval) != 0;
-    constexpr int SEG = kX / G;
-    constexpr int NS = SEG + 1;
-    float Wr[NS * G];
+template <class Sink>
+__device__ __forceinline__ void eval1(float2 *B, Sink &sk, const float2 *Va, int wi,
+                                      const float *s_inv) {
+    const float ia = s_inv[wi];
+    const float2 ia2 = make_float2(ia, ia);
 #pragma unroll
-    for (int s = 0; s < SEG - 1; ++s)
-#pragma unroll
-        for (int e = 0; e < G; ++e) Wr[s * G + e] = ld_t(sg_t, R, r.off + s * G + e);
+    for (int j = 0; j < kX / 2; ++j) {
+        B[j] = add2(B[j], Va[j]);
+        sk.one(j, wi, mul2(B[j], ia2));
+    }
+}
 
-    for (int c0 = 0; c0 < r.count; c0 += 2 * NS) {
+// Fine group (step 1) whose start is a multiple of 16.  For 16 widths c0 + cc
+// the steps are y[16t + q0 + cc + k], k < 16, q0 = off + c0: even cc read the
+// pairs E[q] = positions (2q, 2q+1), odd cc the pairs O[q] = (2q+1, 2q+2).
+template <class Sink>
+__device__ __forceinline__ void run_fine_aligned(float2 *B, Sink &sk, const float *bt,
+                                                 const Group &g, const float *s_inv) {
+    for (int c0 = 0; c0 < g.count; c0 += 16) {
+        const float *blk = bt + kPad * ((g.off + c0) >> 4);
+        float2 E[16], O[15];
+        // widths cc < 8 read E[0..11) and O[0..11); the rest is loaded after
 #pragma unroll
-        for (int u = 0; u < 2 * NS; u += 2) {
-            const int c = c0 + u;
-            if (c >= r.count) break;
-            const bool two = (c + 1 < r.count);
-            // segment c + SEG - 1 -> slot (u + SEG - 1) % NS
+        for (int v = 0; v < 6; ++v) {
+            const float4 f = *reinterpret_cast<const float4 *>(blk + (v >> 2) * kPad + (v & 3) * 4);
+            E[2 * v] = make_float2(f.x, f.y);
+            E[2 * v + 1] = make_float2(f.z, f.w);
+        }
 #pragma unroll
-            for (int e = 0; e < G; ++e)
-                Wr[((u + SEG - 1) % NS) * G + e] = ld_t(sg_t, R, r.off + (c + SEG - 1) * G + e);
-            if (two) {
+        for (int q = 0; q < 11; ++q) O[q] = make_float2(blk[padr(2 * q + 1)], blk[padr(2 * q + 2)]);
 #pragma unroll
-                for (int e = 0; e < G; ++e)
-                    Wr[((u + SEG) % NS) * G + e] = ld_t(sg_t, R, r.off + (c + SEG) * G + e);
+        for (int cc = 0; cc < 16; cc += 2) {
+            if (cc == 8) {
+#pragma unroll
+                for (int v = 6; v < 8; ++v) {
+                    const float4 f =
+                        *reinterpret_cast<const float4 *>(blk + (v >> 2) * kPad + (v & 3) * 4);
+                    E[2 * v] = make_float2(f.x, f.y);
+                    E[2 * v + 1] = make_float2(f.z, f.w);
+                }
+#pragma unroll
+                for (int q = 11; q < 15; ++q)
+                    O[q] = make_float2(blk[padr(2 * q + 1)], blk[padr(2 * q + 2)]);
             }
-            if (eval) {
-                const int wi = r.widx0 + c;
-                const float i0 = s_inv[wi];
-                const uint32_t k0 = 63u - (uint32_t)(wi & 63);
-                if (two) {
-                    const float i1 = s_inv[wi + 1];
-                    const uint32_t k1 = 63u - (uint32_t)((wi + 1) & 63);
+            const int c = c0 + cc;
+            if (c + 1 < g.count)
+                eval2(B, sk, E + cc / 2, O + cc / 2, g.widx0 + c, s_inv);
+            else if (c < g.count)
+                eval1(B, sk, E + cc / 2, g.widx0 + c, s_inv);
+        }
+    }
+}
+
+// Coarse group (step G = 8 or 16) whose start is a multiple of 16.  Width c
+// reads S_G at 16t + off + cG + k, k < 16: SEG = 16/G segments of G positions,
+// kept in a ring of SEG + 1 slots so each segment is loaded once; 2 (SEG + 1)
+// widths per iteration keep every offset a compile-time constant.
+template <int G, class Sink>
+__device__ __forceinline__ void run_coarse_aligned(float2 *B, Sink &sk, const float *bt,
+                                                   const Group &g, const float *s_inv) {
+    constexpr int SEG = 16 / G;
+    constexpr int NS = SEG + 1;
+    constexpr int U = 2 * NS;
+    constexpr int PV = G / 2;          // float2 per segment
+    float2 ring[NS][PV];
+    const float *b0 = bt + kPad * (g.off >> 4);
 #pragma unroll
-                    for (int k = 0; k < kX; ++k) {
-                        st.B[k] += Wr[((u + k / G) % NS) * G + (k % G)];
-                        const float s0 = st.B[k] * i0;
-                        st.B[k] += Wr[((u + 1 + k / G) % NS) * G + (k % G)];
-                        const float s1 = st.B[k] * i1;
-                        st.best[k] = fmax3(st.best[k], packw(s0, k0), packw(s1, k1));
+    for (int m = 0; m < SEG - 1; ++m) {
+#pragma unroll
+        for (int v = 0; v < G / 4; ++v) {
+            const float4 f = *reinterpret_cast<const float4 *>(
+                b0 + kPad * (m / SEG) + G * (m % SEG) + 4 * v);
+            ring[m][2 * v] = make_float2(f.x, f.y);
+            ring[m][2 * v + 1] = make_float2(f.z, f.w);
+        }
+    }
+    for (int c0 = 0; c0 < g.count; c0 += U) {
+        const float *bi = b0 + kPad * (c0 / SEG);
+#pragma unroll
+        for (int u = 0; u < U; u += 2) {
+            const int c = c0 + u;
+            if (c >= g.count) break;
+            const bool two = c + 1 < g.count;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && !two) break;
+                const int m = u + h + SEG - 1;           // segment to bring in
+#pragma unroll
+                for (int v = 0; v < G / 4; ++v) {
+                    const float4 f = *reinterpret_cast<const float4 *>(
+                        bi + kPad * (m / SEG) + G * (m % SEG) + 4 * v);
+                    ring[m % NS][2 * v] = make_float2(f.x, f.y);
+                    ring[m % NS][2 * v + 1] = make_float2(f.z, f.w);
+                }
+            }
+            float2 Va[kX / 2], Vb[kX / 2];
+#pragma unroll
+            for (int j = 0; j < kX / 2; ++j) {
+                Va[j] = ring[(u + j / PV) % NS][j % PV];
+                Vb[j] = ring[(u + 1 + j / PV) % NS][j % PV];
+            }
+            if (two)
+                eval2(B, sk, Va, Vb, g.widx0 + c, s_inv);
+            else
+                eval1(B, sk, Va, g.widx0 + c, s_inv);
+        }
+    }
+}
+
+// Any group, one width at a time with per-step loads (start not a multiple of
+// 16, or the compact recovery pass).  The running sums see the same additions
+// in the same order as in the unrolled paths, so the SNRs are bitwise equal.
+template <class Sink>
+__device__ __forceinline__ void run_generic(float2 *B, Sink &sk, const float *bt, const Group &g,
+                                            int d, const float *s_inv) {
+#pragma unroll 1
+    for (int c = 0; c < g.count; ++c) {
+        const int p0 = g.off + c * d;
+        float2 V[kX / 2];
+#pragma unroll
+        for (int j = 0; j < kX / 2; ++j)
+            V[j] = make_float2(bt[padr(p0 + 2 * j)], bt[padr(p0 + 2 * j + 1)]);
+        eval1(B, sk, V, g.widx0 + c, s_inv);
+    }
+}
+
+// Sum of the block sums of blocks b0 .. b1-1, Kahan-compensated in block order.
+__device__ __forceinline__ float blocks_sum(const float *s_bs, int b0, int b1) {
+    float sum = 0.f, comp = 0.f;
+    for (int b = b0; b < b1; ++b) {
+        const float y = __fsub_rn(s_bs[b], comp);
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+    }
+    return sum;
+}
+
+// Sum of the first q samples of block b.
+__device__ __forceinline__ float block_part(const float *s_y, int b, int q) {
+    float part = 0.f;
+    for (int i = 0; i < q; ++i) part = __fadd_rn(part, s_y[kPad * b + i]);
+    return part;
+}
+
+// Start sums of a group for the thread's 16 samples (thread t, samples 16t+k):
+// B_off(16t + k) = y[16t + k] + ... + y[16t + k + off - 1], taken as the sum
+// of whole blocks between the two positions plus the partial sums inside the
+// blocks at each end.
+__device__ __forceinline__ void group_start(float2 *B, const float *s_y, const float *s_bs,
+                                            int t, int off) {
+    if (off == 0) {
+#pragma unroll
+        for (int j = 0; j < kX / 2; ++j) B[j] = make_float2(0.f, 0.f);
+    } else if ((off & 15) == 0) {
+        const int ta = t + (off >> 4);
+        const float d = blocks_sum(s_bs, t, ta);
+        const float *ya = s_y + kPad * ta;
+        const float *y0 = s_y + kPad * t;
+        float pa = 0.f, p0 = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 fa = *reinterpret_cast<const float4 *>(ya + 4 * v);
+            const float4 f0 = *reinterpret_cast<const float4 *>(y0 + 4 * v);
+            float2 r;
+            r.x = __fadd_rn(d, __fsub_rn(pa, p0));
+            pa = __fadd_rn(pa, fa.x); p0 = __fadd_rn(p0, f0.x);
+            r.y = __fadd_rn(d, __fsub_rn(pa, p0));
+            pa = __fadd_rn(pa, fa.y); p0 = __fadd_rn(p0, f0.y);
+            B[2 * v] = r;
+            r.x = __fadd_rn(d, __fsub_rn(pa, p0));
+            pa = __fadd_rn(pa, fa.z); p0 = __fadd_rn(p0, f0.z);
+            r.y = __fadd_rn(d, __fsub_rn(pa, p0));
+            pa = __fadd_rn(pa, fa.w); p0 = __fadd_rn(p0, f0.w);
+            B[2 * v + 1] = r;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kX / 2; ++j) {
+            float v2x, v2y;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int p = 16 * t + 2 * j + h, q = p + off;
+                const float whole = blocks_sum(s_bs, p >> 4, q >> 4);
+                const float v = __fadd_rn(whole, __fsub_rn(block_part(s_y, q >> 4, q & 15),
+                                                           block_part(s_y, p >> 4, p & 15)));
+                if (h == 0) v2x = v; else v2y = v;
+            }
+            B[j] = make_float2(v2x, v2y);
+        }
+    }
+}
+
+template <int G, class Sink>
+__device__ __forceinline__ void run_group(float2 *B, Sink &sk, const float *sy_t,
+                                          const float *sg_t, const Group &g, const float *s_inv) {
+    const bool aligned = (g.off & 15) == 0;
+    if (G > 1 && (g.flags & kGroupCoarse)) {
+        if (aligned)
+            run_coarse_aligned<(G > 1 ? G : 8)>(B, sk, sg_t, g, s_inv);
+        else
+            run_generic(B, sk, sg_t, g, G, s_inv);
+    } else {
+        if (aligned)
+            run_fine_aligned(B, sk, sy_t, g, s_inv);
+        else
+            run_generic(B, sk, sy_t, g, 1, s_inv);
+    }
+}
+
+// Compact evaluation of a group (recovery of the winning width).
+template <int G, class Sink>
+__device__ __forceinline__ void run_group_compact(float2 *B, Sink &sk, const float *sy_t,
+                                                  const float *sg_t, const Group &g,
+                                                  const float *s_inv) {
+    if (G > 1 && (g.flags & kGroupCoarse))
+        run_generic(B, sk, sg_t, g, G, s_inv);
+    else
+        run_generic(B, sk, sy_t, g, 1, s_inv);
+}
+
+template <int G>
+__device__ __forceinline__ int group_step(const Group &g) {
+    return (G > 1 && (g.flags & kGroupCoarse)) ? G : 1;
+}
+
+// One pass over the window's 16-position blocks: S_G[p] = y[p] + ... + y[p+G-1]
+// (when G > 1; the first of a block by pairwise sums, the next 15 by sliding
+// the window one sample), and per block b its sum s_bs[b] and the largest /
+// smallest prefix C over its 16 positions (s_mx / s_mn, FP32, used only for
+// bounds; C from an FP32 scan of the block sums).  Ends with a barrier.
+template <int G>
+__device__ void build_stats(const float *s_y, float *s_g, float *s_bs, float *s_mx, float *s_mn,
+                            float *s_wt, int R) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll 1
+    for (int r = 0; r * kThreads < R; ++r) {
+        const int c = r * kThreads + tid;
+        float sum = 0.f, hi = 0.f, lo = 0.f;
+        if (c < R) {
+            float v[32];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = *reinterpret_cast<const float4 *>(s_y + kPad * c + 4 * q);
+                v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                if (q) { hi = fmaxf(hi, sum); lo = fminf(lo, sum); }
+                sum = __fadd_rn(sum, v[q]);
+            }
+            if (G > 1) {
+                if (c < R - 1) {
+#pragma unroll
+                    for (int q = 4; q < 8; ++q) {
+                        const float4 f =
+                            *reinterpret_cast<const float4 *>(s_y + kPad * (c + 1) + 4 * (q - 4));
+                        v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
                     }
+                    float w[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) w[q] = v[q];
+#pragma unroll
+                    for (int len = 1; len < G; len *= 2) {
+#pragma unroll
+                        for (int q = 0; q + len < G; q += 2 * len) w[q] = __fadd_rn(w[q], w[q + len]);
+                    }
+                    float o[16];
+                    o[0] = w[0];
+#pragma unroll
+                    for (int q = 1; q < 16; ++q)
+                        o[q] = __fadd_rn(__fsub_rn(o[q - 1], v[q - 1]), v[q - 1 + G]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4 *>(s_g + kPad * c + 4 * q) =
+                            make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < kX; ++k) {
-                        st.B[k] += Wr[((u + k / G) % NS) * G + (k % G)];
-                        st.best[k] = fmaxf(st.best[k], packw(st.B[k] * i0, k0));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < kX; ++k) st.B[k] += Wr[((u + k / G) % NS) * G + (k % G)];
-                if (two) {
-#pragma unroll
-                    for (int k = 0; k < kX; ++k)
-                        st.B[k] += Wr[((u + 1 + k / G) % NS) * G + (k % G)];
+                    for (int q = 0; q < 16; ++q) s_g[kPad * c + q] = -INFINITY;
                 }
             }
+            s_bs[c] = sum;
+            s_mx[c] = hi;   // relative to the block start until the scan below
+            s_mn[c] = lo;
         }
+        // inclusive warp scan of the block sums (FP32, for bounds only)
+        float x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) s_wt[r * (kThreads / 32) + warp] = x;
+        const float xe = __shfl_up_sync(0xffffffffu, x, 1);
+        if (c < R) s_wt[3 * (kThreads / 32) + c] = lane ? xe : 0.f;   // exclusive in warp
     }
+    __syncthreads();
+#pragma unroll 1
+    for (int c = tid; c < R; c += kThreads) {
+        float before = 0.f;
+        const int chunk = c >> 5;   // warp chunk of 32 blocks
+        for (int w = 0; w < chunk; ++w) before += s_wt[w];
+        const float P = before + s_wt[3 * (kThreads / 32) + c];   // C at the block start
+        s_mx[c] += P;
+        s_mn[c] += P;
+    }
+    __syncthreads();
 }
 
-// Build S_G over all positions of the tile's shared window: chunk c holds
-// positions 16c .. 16c+15; S_G[p] = y[p] + ... + y[p+G-1] by pairwise levels.
-template <int G>
-__device__ __forceinline__ void build_sg(const float *s_y, float *s_g, int R) {
-    for (int c = threadIdx.x; c < R - 1; c += kThreads) {
-        float v[kX + G - 1];
-#pragma unroll
-        for (int m = 0; m < kX + G - 1; ++m) v[m] = s_y[(m & (kX - 1)) * R + c + (m >> 4)];
-#pragma unroll
-        for (int len = 1; len < G; len *= 2) {
-#pragma unroll
-            for (int m = 0; m < kX + G - 1 - len; ++m) v[m] = v[m] + v[m + len];
-        }
-#pragma unroll
-        for (int m = 0; m < kX; ++m) s_g[m * R + c] = v[m];
+// Largest 1/sigma_w of each group (for the bounds of the candidate search).
+__device__ __forceinline__ void group_inv_max(const Program &prog, const float *s_inv,
+                                              float *s_ginv) {
+    for (int gi = threadIdx.x; gi < prog.n_groups; gi += kThreads) {
+        const Group g = prog.groups[gi];
+        float mxv = 0.f;
+        for (int c = 0; c < g.count; ++c) mxv = fmaxf(mxv, s_inv[g.widx0 + c]);
+        s_ginv[gi] = mxv;
     }
-    // last column: positions past the window are never read by an evaluated
-    // width; fill with -inf for determinism.
-    if (threadIdx.x < kX) s_g[threadIdx.x * R + (R - 1)] = -INFINITY;
 }
 
 template <int DT, int G, bool PLANE, bool MG>
 __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
                                                              const __grid_constant__ Program prog) {
     using T = typename Elem<DT>::T;
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int R = a.R;
-    float *s_y = smem;
-    float *s_g = s_y + kX * R;
-    float *s_inv = s_y + (G > 1 ? 2 : 1) * kX * R;
+    uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem);
+    unsigned char *s_raw0 = smem + 16;
+    float *s_y = reinterpret_cast<float *>(s_raw0 + 2 * a.raw_bytes);
+    float *s_g = s_y + kPad * R;
+    float *s_bs = s_y + (G > 1 ? 2 : 1) * kPad * R;
+    float *s_mx = s_bs + R;
+    float *s_mn = s_mx + R;
+    float *s_inv = s_mn + R;
+    float *s_ginv = s_inv + prog.n_eval;
     __shared__ int s_wsum[kThreads / 32];
     __shared__ unsigned long long s_base;
+    __shared__ float s_wt[3 * (kThreads / 32) + 3 * kThreads];
 
     const int tid = threadIdx.x;
-    const int64_t row = blockIdx.x / a.tiles_per_row;
-    const int64_t t0 = (blockIdx.x - row * a.tiles_per_row) * (int64_t)kTile;
-    const int entry = a.per_row ? (int)row : 0;
-    const int64_t i0 = t0 + (int64_t)tid * kX;   // first start sample of this thread
+    const int64_t n_tiles = a.n_dm * a.tiles_per_row;
+    const int span = a.span;
+    const bool tma = a.vec_ok != 0;
+    const int64_t esz = (int64_t)sizeof(T);
 
-    if (a.flags[entry]) {
-        if (PLANE) {
-            for (int k = 0; k < kX; ++k) {
-                if (i0 + k < a.n_samp) {
-                    a.snr_out[row * a.out_stride + i0 + k] = __int_as_float(0x7fc00000);
-                    a.width_out[row * a.out_stride + i0 + k] = 0;
-                }
-            }
+    if (tma) {
+        if (tid == 0) {
+            mbar_init(s_bar);
+            mbar_init(s_bar + 1);
+            fence_mbar_init();
         }
-        return;
-    }
-
-    for (int k = tid; k < prog.n_eval; k += kThreads)
-        s_inv[k] = a.inv_tab[(int64_t)entry * prog.n_eval + k];
-    const float2 mu = a.mu_tab[entry];
-    const bool has_sc = a.scale != nullptr;
-    const float sc = has_sc ? a.scale[row] : 1.f;
-    const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
-    const T *rowp = static_cast<const T *>(a.data) + row * a.stride;
-    const int span = kTile + prog.wmax - 1;   // positions [0, span) of the window are needed
-
-    // Stage centred samples; -inf past the row end (and past the window).
-    for (int q = tid; q < (kX * R) / 4; q += kThreads) {
-        const int p = 4 * q;
-        const int64_t gt = t0 + p;
-        float x[4];
-        if (a.vec_ok && gt + 3 < a.n_samp && p + 3 < span) {
-            load4v<DT>(rowp + gt, x[0], x[1], x[2], x[3]);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (has_sc) x[e] = fmaf(sc, x[e], of);
-                x[e] = (x[e] - mu.x) - mu.y;
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (gt + e < a.n_samp && p + e < span) {
-                    float v = Elem<DT>::cvt(rowp[gt + e]);
-                    if (has_sc) v = fmaf(sc, v, of);
-                    x[e] = (v - mu.x) - mu.y;
-                } else {
-                    x[e] = -INFINITY;
-                }
-            }
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) s_y[((p + e) & (kX - 1)) * R + ((p + e) >> 4)] = x[e];
-    }
-    __syncthreads();
-    if (G > 1) {
-        build_sg<(G > 1 ? G : 2)>(s_y, s_g, R);
         __syncthreads();
     }
+    // bulk copy of tile `tile`'s window into raw buffer `buf` (thread 0 only)
+    auto issue = [&](int64_t tile, int buf) {
+        const int64_t row = tile / a.tiles_per_row;
+        const int64_t t0 = (tile - row * a.tiles_per_row) * (int64_t)kTile;
+        const int64_t have = min((int64_t)span, a.n_samp - t0);
+        const uint32_t nb = (uint32_t)((have * esz) & ~(int64_t)15);
+        uint64_t *bar = s_bar + buf;
+        fence_proxy_async();
+        mbar_expect(bar, nb);
+        if (nb) {
+            const T *src = static_cast<const T *>(a.data) + row * a.stride + t0;
+            bulk_load(s_raw0 + buf * a.raw_bytes, src, nb, bar);
+        }
+    };
+    if (tma && tid == 0 && (int64_t)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
+    if (!a.per_row) {   // one MSD for the whole plane: constants once per CTA
+        for (int q = tid; q < prog.n_eval; q += kThreads) s_inv[q] = a.inv_tab[q];
+        __syncthreads();
+        if (!PLANE) group_inv_max(prog, s_inv, s_ginv);
+        // visible after the first tile's staging barrier
+    }
 
-    State st;
-    float obest[MG ? kX : 1];
-    int ogrp[MG ? kX : 1];
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        const int64_t row = tile / a.tiles_per_row;
+        const int64_t t0 = (tile - row * a.tiles_per_row) * (int64_t)kTile;
+        const int entry = a.per_row ? (int)row : 0;
+        const int64_t i0 = t0 + (int64_t)tid * kX;   // first start sample of this thread
+        const T *rowp = static_cast<const T *>(a.data) + row * a.stride;
+
+        if (tma && !mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1))) {
+            // the copy did not land in time: report it, give the copy one more
+            // bounded wait, and leave this CTA
+            if (tid == 0) {
+                if (a.result) atomicExch(&a.result->status, (int)SPD_ERR_TIMEOUT);
+                mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+            }
+            return;
+        }
+
+        const bool deg = a.flags[entry] != 0;
+        const float2 mu = a.mu_tab[entry];
+        const bool has_sc = a.scale != nullptr;
+        const float sc = has_sc ? a.scale[row] : 1.f;
+        const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
+        const int64_t have = min((int64_t)span, a.n_samp - t0);
+        const int nraw = tma ? (int)(((have * esz) & ~(int64_t)15) / esz) : 0;
+        const T *raw = reinterpret_cast<const T *>(s_raw0 + buf * a.raw_bytes);
+
+        if (!deg) {
+            if (a.per_row)
+                for (int q = tid; q < prog.n_eval; q += kThreads)
+                    s_inv[q] = a.inv_tab[(int64_t)entry * prog.n_eval + q];
+            // Stage centred samples; -inf past the row end and past the window.
+            for (int q = tid; q < 4 * R; q += kThreads) {
+                const int p = 4 * q;
+                float x[4];
+                if (p + 3 < nraw) {
+                    load4v<DT>(raw + p, x[0], x[1], x[2], x[3]);
+                } else {
 #pragma unroll
-    for (int k = 0; k < kX; ++k) {
-        st.B[k] = 0.f;
-        st.best[k] = -INFINITY;
-    }
-    if (MG) {
+                    for (int e = 0; e < 4; ++e)
+                        x[e] = (p + e < nraw)  ? Elem<DT>::cvt(raw[p + e])
+                               : (p + e < have) ? Elem<DT>::cvt(rowp[t0 + p + e])
+                                                : -INFINITY;
+                }
 #pragma unroll
-        for (int k = 0; k < kX; ++k) { obest[k] = -INFINITY; ogrp[k] = 0; }
-    }
-    const float *sy_t = s_y + tid;
-    const float *sg_t = s_g + tid;
-    for (int ri = 0; ri < prog.n_runs; ++ri) {
-        const Run r = prog.runs[ri];
-        if (G > 1 && (r.flags & kRunSrcG))
-            run_coarse<(G > 1 ? G : 2)>(st, sg_t, R, r, s_inv);
-        else
-            run_fine(st, sy_t, R, r, s_inv);
-        if (MG && (r.flags & kRunEndGroup)) {
-            const int g = r.widx0 >> 6;
-#pragma unroll
-            for (int k = 0; k < kX; ++k) {
-                if (st.best[k] > obest[k]) { obest[k] = st.best[k]; ogrp[k] = g; }
-                st.best[k] = -INFINITY;
+                for (int e = 0; e < 4; ++e) {
+                    if (p + e < have) {
+                        if (has_sc) x[e] = fmaf(sc, x[e], of);
+                        x[e] = __fsub_rn(__fsub_rn(x[e], mu.x), mu.y);
+                    } else {
+                        x[e] = -INFINITY;
+                    }
+                }
+                *reinterpret_cast<float4 *>(s_y + padr(p)) = make_float4(x[0], x[1], x[2], x[3]);
             }
         }
-    }
+        __syncthreads();
+        // the raw buffer is free again: prefetch the window of the tile after
+        if (tma && tid == 0 && tile + gridDim.x < n_tiles) issue(tile + gridDim.x, buf ^ 1);
 
-    // Decode (value, width) and emit.
-    float snr[kX];
-    int wdt[kX];
-#pragma unroll
-    for (int k = 0; k < kX; ++k) {
-        const float bv = MG ? obest[k] : st.best[k];
-        const uint32_t bits = __float_as_uint(bv);
-        const int g = MG ? ogrp[k] : 0;
-        const int wi = g * 64 + (63 - (int)(bits & 63u));
-        snr[k] = __uint_as_float(bits & 0xFFFFFFC0u);
-        wdt[k] = (wi < prog.n_eval) ? (int)prog.eval_w[wi] : 0;
-    }
-
-    if (PLANE) {
-        float *so = a.snr_out + row * a.out_stride;
-        uint16_t *wo = a.width_out + row * a.out_stride;
-        const bool full = i0 + kX <= a.n_samp;
-        const bool al = ((reinterpret_cast<uintptr_t>(so + i0) & 15) == 0) &&
-                        ((reinterpret_cast<uintptr_t>(wo + i0) & 15) == 0);
-        if (full && al) {
-#pragma unroll
-            for (int v = 0; v < kX / 4; ++v)
-                reinterpret_cast<float4 *>(so + i0)[v] =
-                    make_float4(snr[4 * v], snr[4 * v + 1], snr[4 * v + 2], snr[4 * v + 3]);
-#pragma unroll
-            for (int v = 0; v < kX / 8; ++v) {
-                uint4 u;
-                u.x = (uint32_t)wdt[8 * v] | ((uint32_t)wdt[8 * v + 1] << 16);
-                u.y = (uint32_t)wdt[8 * v + 2] | ((uint32_t)wdt[8 * v + 3] << 16);
-                u.z = (uint32_t)wdt[8 * v + 4] | ((uint32_t)wdt[8 * v + 5] << 16);
-                u.w = (uint32_t)wdt[8 * v + 6] | ((uint32_t)wdt[8 * v + 7] << 16);
-                reinterpret_cast<uint4 *>(wo + i0)[v] = u;
+        if (deg) {
+            if (PLANE) {
+                for (int q = 0; q < kX; ++q) {
+                    if (i0 + q < a.n_samp) {
+                        a.snr_out[row * a.out_stride + i0 + q] = __int_as_float(0x7fc00000);
+                        a.width_out[row * a.out_stride + i0 + q] = 0;
+                    }
+                }
             }
-        } else {
+            continue;   // uniform across the CTA
+        }
+
+        build_stats<G>(s_y, s_g, s_bs, s_mx, s_mn, s_wt, R);   // ends with a barrier
+        if (!PLANE && a.per_row) {
+            group_inv_max(prog, s_inv, s_ginv);
+            __syncthreads();
+        }
+
+        const float *sy_t = s_y + kPad * tid;
+        const float *sg_t = s_g + kPad * tid;
+        float2 B[kX / 2];
+        float snr[kX];
+        int wdt[kX];
+        if (PLANE) {
+            float obest[MG ? kX : 1];
+            int ogrp[MG ? kX : 1];
+            if (MG) {
 #pragma unroll
-            for (int k = 0; k < kX; ++k) {
-                if (i0 + k < a.n_samp) {
-                    so[i0 + k] = snr[k];
-                    wo[i0 + k] = (uint16_t)wdt[k];
+                for (int q = 0; q < kX; ++q) { obest[q] = -INFINITY; ogrp[q] = 0; }
+            }
+            PackSink sk;
+            float *best = sk.best;
+#pragma unroll
+            for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
+            int cur = 0;   // block of 64 eval indices being packed
+            for (int gi = 0; gi < prog.n_groups; ++gi) {
+                const Group g = prog.groups[gi];
+                if (MG && (g.widx0 >> 6) != cur) {
+                    // blocks of 64 widths: a later block wins only with a larger
+                    // value (its code bits say nothing about earlier blocks)
+#pragma unroll
+                    for (int q = 0; q < kX; ++q) {
+                        if (trunc17(best[q]) > trunc17(obest[q]) || obest[q] != obest[q]) {
+                            obest[q] = best[q];
+                            ogrp[q] = cur;
+                        }
+                        best[q] = -INFINITY;
+                    }
+                    cur = g.widx0 >> 6;
+                }
+                group_start(B, s_y, s_bs, tid, g.off);
+                run_group<G>(B, sk, sy_t, sg_t, g, s_inv);
+            }
+            if (MG) {
+#pragma unroll
+                for (int q = 0; q < kX; ++q)
+                    if (trunc17(best[q]) > trunc17(obest[q]) || obest[q] != obest[q]) {
+                        obest[q] = best[q];
+                        ogrp[q] = cur;
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < kX; ++q) {
+                const float bv = MG ? obest[q] : best[q];
+                const uint32_t bits = __float_as_uint(bv);
+                const int wi = (MG ? ogrp[q] : 0) * 64 + (63 - (int)(bits & 63u));
+                snr[q] = __uint_as_float(bits & 0xFFFFFFC0u);
+                wdt[q] = (wi < prog.n_eval) ? (int)prog.eval_w[wi] : 0;
+            }
+            float *so = a.snr_out + row * a.out_stride;
+            uint16_t *wo = a.width_out + row * a.out_stride;
+            const bool full = i0 + kX <= a.n_samp;
+            const bool al = ((reinterpret_cast<uintptr_t>(so + i0) & 15) == 0) &&
+                            ((reinterpret_cast<uintptr_t>(wo + i0) & 15) == 0);
+            if (full && al) {
+#pragma unroll
+                for (int v = 0; v < kX / 4; ++v)
+                    reinterpret_cast<float4 *>(so + i0)[v] =
+                        make_float4(snr[4 * v], snr[4 * v + 1], snr[4 * v + 2], snr[4 * v + 3]);
+#pragma unroll
+                for (int v = 0; v < kX / 8; ++v) {
+                    uint4 u;
+                    u.x = (uint32_t)wdt[8 * v] | ((uint32_t)wdt[8 * v + 1] << 16);
+                    u.y = (uint32_t)wdt[8 * v + 2] | ((uint32_t)wdt[8 * v + 3] << 16);
+                    u.z = (uint32_t)wdt[8 * v + 4] | ((uint32_t)wdt[8 * v + 5] << 16);
+                    u.w = (uint32_t)wdt[8 * v + 6] | ((uint32_t)wdt[8 * v + 7] << 16);
+                    reinterpret_cast<uint4 *>(wo + i0)[v] = u;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kX; ++q) {
+                    if (i0 + q < a.n_samp) {
+                        so[i0 + q] = snr[q];
+                        wo[i0 + q] = (uint16_t)wdt[q];
+                    }
+                }
+            }
+            __syncthreads();   // shared arrays are rewritten by the next tile
+            continue;
+        }
+
+        // ------------------------------------------------ candidate search
+        const float thr = a.threshold;
+        const float minC = s_mn[tid];
+        FindSink fk;
+        float *best = fk.best;
+#pragma unroll
+        for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
+        MaxSink mk;
+        float minbest = -INFINITY;   // smallest current best of the 16 samples
+        for (int gi = prog.n_groups - 1; gi >= 0; --gi) {
+            const Group g = prog.groups[gi];
+            const int d = group_step<G>(g);
+            // upper bound over the thread's 16 samples and the group's widths
+            const int jb0 = tid + ((g.off + d) >> 4);
+            const int jb1 = tid + ((15 + g.off + g.count * d) >> 4);
+            float rmax = -INFINITY;
+            for (int jb = jb0; jb <= jb1; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
+            const float lim = fmaxf(thr, minbest);
+            const float ub = __fsub_rn(rmax, minC);
+            const float slack = 1e-5f * (fabsf(rmax) + fabsf(minC)) + 1e-30f;
+            const float bound = ub > 0.f ? (ub + slack) * s_ginv[gi] * 1.00001f : 0.f;
+            // a NaN bound (window past the row end) falls through to evaluation
+            if (bound + 1e-5f * fabsf(lim) < lim) continue;
+            mk.reset();
+            group_start(B, s_y, s_bs, tid, g.off);
+            run_group<G>(B, mk, sy_t, sg_t, g, s_inv);
+            const uint32_t code = 63u - (uint32_t)gi;
+#pragma unroll
+            for (int q = 0; q < kX; ++q) best[q] = fmaxf(best[q], packw(mk.m[q], code));
+            minbest = best[0];
+#pragma unroll
+            for (int q = 1; q < kX; ++q) minbest = fminf(minbest, best[q]);
+        }
+
+        // candidates and their winning groups
+        uint32_t mask = 0;
+        uint64_t need = 0;
+#pragma unroll
+        for (int q = 0; q < kX; ++q) {
+            fk.found[q] = -1;
+            if (i0 + q < a.n_samp && trunc17(best[q]) >= thr) {
+                mask |= 1u << q;
+                need |= 1ull << (63u - (__float_as_uint(best[q]) & 63u));
+            }
+        }
+        // recovery: re-evaluate each winning group with the same arithmetic
+        while (need) {
+            const int gi = __ffsll((long long)need) - 1;
+            need &= need - 1;
+            const Group g = prog.groups[gi];
+            fk.code = 63u - (uint32_t)gi;
+            group_start(B, s_y, s_bs, tid, g.off);
+            run_group_compact<G>(B, fk, sy_t, sg_t, g, s_inv);
+        }
+#pragma unroll
+        for (int q = 0; q < kX; ++q) {
+            snr[q] = trunc17(best[q]);
+            wdt[q] = fk.found[q] >= 0 ? (int)prog.eval_w[fk.found[q]] : 0;
+        }
+
+        // Threshold (Sec. 2.4, inclusive) and block-aggregated compaction.
+        const int cnt = __popc(mask);
+        const int lane = tid & 31, warp = tid >> 5;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (tid < 32) {
+            const int wv = (lane < kThreads / 32) ? s_wsum[lane] : 0;
+            int wsc = wv;
+#pragma unroll
+            for (int o = 1; o < kThreads / 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, wsc, o);
+                if (lane >= o) wsc += v;
+            }
+            if (lane < kThreads / 32) s_wsum[lane] = wsc - wv;   // exclusive
+            const int total = __shfl_sync(0xffffffffu, wsc, kThreads / 32 - 1);
+            if (lane == 0)
+                s_base = total ? atomicAdd(reinterpret_cast<unsigned long long *>(&a.result->count),
+                                           (unsigned long long)total)
+                               : 0ull;
+        }
+        __syncthreads();
+        if (cnt) {
+            unsigned long long idx = s_base + (unsigned long long)(s_wsum[warp] + incl - cnt);
+#pragma unroll
+            for (int q = 0; q < kX; ++q) {
+                if (mask & (1u << q)) {
+                    if (idx < (unsigned long long)a.capacity) {
+                        int4 rec;
+                        rec.x = (int)row;
+                        rec.y = (int)(i0 + q);
+                        rec.z = __float_as_int(snr[q]);
+                        rec.w = wdt[q];
+                        reinterpret_cast<int4 *>(a.out)[idx] = rec;
+                    }
+                    ++idx;
                 }
             }
         }
-        return;
-    }
-
-    // Threshold (Sec. 2.4, inclusive) and block-aggregated compaction.
-    uint32_t mask = 0;
-#pragma unroll
-    for (int k = 0; k < kX; ++k)
-        if (i0 + k < a.n_samp && snr[k] >= a.threshold) mask |= 1u << k;
-    const int cnt = __popc(mask);
-    const int lane = tid & 31, warp = tid >> 5;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_wsum[warp] = incl;
-    __syncthreads();
-    if (tid < 32) {
-        const int wv = (lane < kThreads / 32) ? s_wsum[lane] : 0;
-        int wi = wv;
-#pragma unroll
-        for (int o = 1; o < kThreads / 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += v;
-        }
-        if (lane < kThreads / 32) s_wsum[lane] = wi - wv;   // exclusive
-        const int total = __shfl_sync(0xffffffffu, wi, kThreads / 32 - 1);
-        if (lane == 0)
-            s_base = total ? atomicAdd(reinterpret_cast<unsigned long long *>(&a.result->count),
-                                       (unsigned long long)total)
-                           : 0ull;
-    }
-    __syncthreads();
-    if (cnt) {
-        unsigned long long idx = s_base + (unsigned long long)(s_wsum[warp] + incl - cnt);
-#pragma unroll
-        for (int k = 0; k < kX; ++k) {
-            if (mask & (1u << k)) {
-                if (idx < (unsigned long long)a.capacity) {
-                    int4 rec;
-                    rec.x = (int)row;
-                    rec.y = (int)(i0 + k);
-                    rec.z = __float_as_int(snr[k]);
-                    rec.w = wdt[k];
-                    reinterpret_cast<int4 *>(a.out)[idx] = rec;
-                }
-                ++idx;
-            }
-        }
+        // no barrier needed here: every warp has passed the emission barriers,
+        // so all reads of this tile's shared arrays are done
     }
 }
 
@@ -414,32 +875,37 @@ template <int DT, int G>
 cudaError_t launch_dg(const DetectArgs &a, const Program &prog, bool plane_out, bool mg,
                       size_t smem, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
-    const dim3 grid((unsigned)tiles);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     void (*k)(const DetectArgs, const Program);
     if (plane_out)
         k = mg ? detect_kernel<DT, G, true, true> : detect_kernel<DT, G, true, false>;
     else
-        k = mg ? detect_kernel<DT, G, false, true> : detect_kernel<DT, G, false, false>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+        k = detect_kernel<DT, G, false, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, kThreads, smem, s>>>(a, prog);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t grid = tiles < (int64_t)sms * per_sm ? tiles : (int64_t)sms * per_sm;
+    k<<<(unsigned)grid, kThreads, smem, s>>>(a, prog);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <int DT>
-cudaError_t launch_detect_dt(const DetectArgs &a, const Program &prog, bool plane_out, size_t smem,
-                     cudaStream_t s) {
+cudaError_t launch_detect_dt(const DetectArgs &a, const Program &prog, bool plane_out,
+                             size_t smem, cudaStream_t s) {
     const bool mg = prog.n_eval > 64;
     switch (prog.G) {
-        case 4: return launch_dg<DT, 4>(a, prog, plane_out, mg, smem, s);
         case 8: return launch_dg<DT, 8>(a, prog, plane_out, mg, smem, s);
         case 16: return launch_dg<DT, 16>(a, prog, plane_out, mg, smem, s);
         default: return launch_dg<DT, 1>(a, prog, plane_out, mg, smem, s);
     }
 }
-
 
 }  // namespace spd

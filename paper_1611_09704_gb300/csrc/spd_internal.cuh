@@ -58,31 +58,35 @@ constexpr int kX = 16;              // consecutive samples owned by one thread
 constexpr int kThreads = 256;       // threads per CTA
 constexpr int kTile = kX * kThreads; // samples of one row searched per CTA
 
-// One run of the boxcar-growing program (host-compiled from the width list).
-// Each step adds one value to every running boxcar sum B: from the centred
-// samples y (src 0, positions off, off+1, ...) or from the G-sample window
-// sums S_G (src 1, positions off, off+G, ...).  If `eval`, every step
-// completes a listed width whose SNR is evaluated, eval index widx0 + step.
-// `end_group`: last evaluating run of a group of 64 eval indices.
-struct Run {
+// One group of evaluated widths (host-compiled from the width list).  The
+// running boxcar sum B of every start sample i starts as
+// B_off(i) = y[i] + ... + y[i+off-1] (read from the tile's compensated prefix
+// sums) and then grows one step per member, as in Algorithm 1: from the
+// centred samples y (step 1, positions off, off+1, ...) or from the G-sample
+// window sums S_G (step G, positions off, off+G, ...).  Member c is the width
+// off + (c+1) * step with eval index widx0 + c.  Groups are evaluated in any
+// order; in the candidate search a group whose upper bound cannot reach the
+// threshold or the current best is skipped.
+struct Group {
     int16_t off;
     int16_t count;
     int16_t widx0;
-    uint16_t flags;   // bit 0: src, bit 1: eval, bit 2: end_group
+    uint16_t flags;   // bit 0: step G (window sums), else step 1
 };
-constexpr uint16_t kRunSrcG = 1, kRunEval = 2, kRunEndGroup = 4;
+constexpr uint16_t kGroupCoarse = 1;
 
-constexpr int kMaxRuns = 512;
+constexpr int kMaxGroups = 512;
+constexpr int kMaxCodeGroups = 64;          // groups a packed max can tell apart
 constexpr int kMaxEval = SPD_MAX_WIDTHS + 1;
 
 // The whole width program, passed by value as a __grid_constant__ kernel
 // parameter so that launching needs no host-to-device copy of its own.
 struct Program {
-    int32_t n_runs;
+    int32_t n_groups;
     int32_t n_eval;     // evaluated widths: width 1 first, then the listed ones
     int32_t wmax;
     int32_t G;          // step of the coarse window sums, 0 if unused
-    Run runs[kMaxRuns];
+    Group groups[kMaxGroups];
     uint16_t eval_w[kMaxEval];
 };
 
@@ -90,12 +94,14 @@ struct DetectArgs {
     const void *data;
     int64_t n_dm, n_samp, stride;
     const float *scale, *offset;
-    int vec_ok;
+    int vec_ok;                 // 16-byte aligned rows: bulk (TMA) copies allowed
     int per_row;                // MSD scope entry = row (else entry 0)
     const float *inv_tab;       // [entries][n_eval]: 1 / sigma_w, FP32
     const float2 *mu_tab;       // [entries]: mean split into hi + lo FP32
     const int32_t *flags;       // [entries]: nonzero = degenerate sigma
-    int R;                      // row length of the transposed shared arrays
+    int R;                      // blocks of 16 positions staged per tile
+    int span;                   // positions of one tile's window (tile + wmax - 1)
+    int raw_bytes;              // bytes of one raw staging buffer (multiple of 16)
     int64_t tiles_per_row;
     float threshold;
     spd_candidate *out;
