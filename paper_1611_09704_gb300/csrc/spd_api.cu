@@ -65,17 +65,20 @@ bool scope_ok(int scope) { return scope == SPD_MSD_GLOBAL || scope == SPD_MSD_PE
 
 struct MsdLayout {
     int64_t upr;           // units per row
-    size_t parts_off, scratch_off, total;
+    int64_t ntpr;          // sigma_Nmax tiles per row (0 when not measured)
+    size_t parts_off, scratch_off, nmax_off, total;
 };
 constexpr int kMergeScratch = 256;
 
-MsdLayout msd_layout(const spd_plane *p) {
+MsdLayout msd_layout(const spd_plane *p, int nmax = 0) {
     MsdLayout l;
     l.upr = p->n_samp > 0 ? (p->n_samp + kMsdUnit - 1) / kMsdUnit : 0;
+    l.ntpr = nmax >= 2 ? nmax_tiles_per_row(p->n_samp) : 0;
     const size_t parts = (size_t)(p->n_dm * l.upr) * sizeof(MsdPart);
     l.parts_off = 0;
     l.scratch_off = align_up(parts);
-    l.total = l.scratch_off + align_up(kMergeScratch * sizeof(MsdPart));
+    l.nmax_off = l.scratch_off + align_up(kMergeScratch * sizeof(MsdPart));
+    l.total = l.nmax_off + align_up((size_t)(p->n_dm * l.ntpr) * sizeof(MsdPart));
     return l;
 }
 
@@ -282,9 +285,9 @@ const char *spd_status_string(int32_t s) {
 int32_t spd_last_cuda_error(void) { return g_last_cuda_error; }
 
 size_t spd_msd_workspace_bytes(const spd_plane *plane, int32_t scope, int32_t nmax_sigma) {
-    (void)nmax_sigma;
     if (check_plane(plane) != SPD_OK || !scope_ok(scope)) return 0;
-    return msd_layout(plane).total;
+    if (nmax_sigma < 0 || nmax_sigma == 1 || nmax_sigma > SPD_MAX_WIDTH) return 0;
+    return msd_layout(plane, nmax_sigma).total;
 }
 
 spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
@@ -293,8 +296,7 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
     if (!scope_ok(scope) || !out_dev) return SPD_ERR_INVALID_ARG;
     if (nmax_sigma < 0 || nmax_sigma == 1 || nmax_sigma > SPD_MAX_WIDTH)
         return SPD_ERR_INVALID_ARG;
-    if (nmax_sigma >= 2) return SPD_ERR_UNSUPPORTED;
-    const MsdLayout L = msd_layout(plane);
+    const MsdLayout L = msd_layout(plane, nmax_sigma);
     SPD_TRY(check_ws(workspace, workspace_bytes, L.total));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(workspace);
@@ -316,6 +318,23 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
     if (scope == SPD_MSD_PER_ROW && plane->n_dm == 0) return SPD_OK;
     SPD_CK(launch_msd_merge(parts, plane->n_dm, L.upr, plane->n_samp,
                             scope == SPD_MSD_PER_ROW, scratch, kMergeScratch, out_dev, st));
+    if (nmax_sigma >= 2 && !plane_empty(plane)) {
+        // sigma_Nmax of Eq. 5, centred on the mean just merged
+        NmaxArgs n;
+        n.data = plane->data;
+        n.n_dm = plane->n_dm;
+        n.n_samp = plane->n_samp;
+        n.stride = plane->row_stride;
+        n.scale = plane->row_scale;
+        n.offset = plane->row_offset;
+        n.msd = out_dev;
+        n.per_row = scope == SPD_MSD_PER_ROW;
+        n.nmax = nmax_sigma;
+        n.nb = nmax_blocks(nmax_sigma);
+        n.tiles_per_row = L.ntpr;
+        n.parts = reinterpret_cast<MsdPart *>(base + L.nmax_off);
+        SPD_CK(launch_nmax(n, plane->dtype, scratch, kMergeScratch, out_dev, st));
+    }
     return SPD_OK;
 }
 
@@ -402,8 +421,8 @@ size_t spd_search_workspace_bytes(const spd_plane *plane, const spd_search_param
     Program prog;
     if (compile_program(params->widths, params->n_widths, prog) != SPD_OK) return 0;
     const int64_t entries = entries_of(plane, params->msd_scope);
-    return msd_layout(plane).total + align_up((size_t)entries * sizeof(spd_msd_stats)) +
-           det_layout(entries, prog.n_eval).total;
+    return msd_layout(plane, nmax_of(params)).total +
+           align_up((size_t)entries * sizeof(spd_msd_stats)) + det_layout(entries, prog.n_eval).total;
 }
 
 spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
@@ -422,7 +441,7 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
         return SPD_OK;
     }
     const int64_t entries = entries_of(plane, params->msd_scope);
-    const MsdLayout ML = msd_layout(plane);
+    const MsdLayout ML = msd_layout(plane, nmax_of(params));
     const size_t msd_bytes = align_up((size_t)entries * sizeof(spd_msd_stats));
     const size_t need = ML.total + msd_bytes + det_layout(entries, prog.n_eval).total;
     SPD_TRY(check_ws(workspace, workspace_bytes, need));

@@ -52,6 +52,19 @@ struct MsdArgs {
     MsdPart *parts;      // [n_dm * units_per_row]
 };
 
+// Arguments of the sigma_Nmax pass (Eq. 5): tiles of 4096 starts per row.
+struct NmaxArgs {
+    const void *data;
+    int64_t n_dm, n_samp, stride;
+    const float *scale, *offset;
+    const spd_msd_stats *msd;   // mean used for centring, per scope entry
+    int per_row;
+    int nmax;
+    int nb;                     // staged blocks of 16 samples per tile
+    int64_t tiles_per_row;
+    MsdPart *parts;             // [n_dm * tiles_per_row]
+};
+
 // ------------------------------------------------------------------ detect
 
 constexpr int kX = 16;              // consecutive samples owned by one thread
@@ -128,6 +141,10 @@ cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t units_p
                              int64_t n_samp, int per_row, MsdPart *scratch, int n_scratch,
                              spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_consts(const ConstArgs &a, const Program &prog, cudaStream_t s);
+int nmax_blocks(int nmax);
+int64_t nmax_tiles_per_row(int64_t n_samp);
+cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
+                        spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_detect(const DetectArgs &a, const Program &prog, int dtype, bool plane_out,
                           size_t smem, cudaStream_t s);
 cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,

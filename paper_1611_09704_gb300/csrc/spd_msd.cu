@@ -307,6 +307,119 @@ __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
     }
 }
 
+// ----------------------------------------------------- sigma_Nmax (Eq. 5)
+
+constexpr int kNmaxTile = 4096;        // start samples per CTA
+constexpr int kNmaxPer = kNmaxTile / kMsdThreads;   // 16 consecutive starts per thread
+
+// Sec. 2.2, Eq. 5 needs sigma_Nmax, the measured sd of the boxcar series
+// B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA stages the
+// centred samples of one tile plus an (Nmax - 1)-sample halo, forms B for its
+// 16 consecutive starts per thread (whole-block sums plus partial sums for the
+// first start, then sliding one sample), and reduces them to (n, T, S) with
+// Eq. 1 per thread and Eq. 2 across lanes and warps.  The sd does not depend
+// on the centring.
+template <int DT>
+__global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArgs a) {
+    using T = typename Elem<DT>::T;
+    extern __shared__ float s_y[];                 // [nb * 16] centred samples
+    float *s_bs = s_y + 16 * a.nb;                 // [nb] block sums
+    const int tid = threadIdx.x;
+    const int64_t row = blockIdx.x / a.tiles_per_row;
+    const int64_t t0 = (blockIdx.x - row * a.tiles_per_row) * (int64_t)kNmaxTile;
+    const int entry = a.per_row ? (int)row : 0;
+    const double mu = a.msd[entry].mean;
+    const float mh = (float)mu, ml = (float)(mu - (double)mh);
+    const T *rp = static_cast<const T *>(a.data) + row * a.stride;
+    const bool has_sc = a.scale != nullptr;
+    const float sc = has_sc ? a.scale[row] : 1.f;
+    const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
+    const int npos = 16 * a.nb;
+    for (int p = tid; p < npos; p += kMsdThreads) {
+        float v = 0.f;
+        if (t0 + p < a.n_samp) {
+            v = Elem<DT>::cvt(rp[t0 + p]);
+            if (has_sc) v = fmaf(sc, v, of);
+            v = (v - mh) - ml;
+        }
+        s_y[p] = v;
+    }
+    __syncthreads();
+    for (int b = tid; b < a.nb; b += kMsdThreads) {
+        float sum = 0.f;
+        for (int q = 0; q < 16; ++q) sum += s_y[16 * b + q];
+        s_bs[b] = sum;
+    }
+    __syncthreads();
+
+    Acc acc;
+    const int nmax = a.nmax;
+    const int p0 = tid * kNmaxPer;                 // first start of this thread (tile-local)
+    // B at p0: whole blocks from p0 to p0 + nmax, corrected by the partial sums
+    // inside the two end blocks (p0 is a multiple of 16)
+    const int qe = p0 + nmax;
+    float whole = 0.f, comp = 0.f;
+    for (int b = p0 >> 4; b < (qe >> 4); ++b) {   // Kahan over whole blocks
+        const float y = s_bs[b] - comp;
+        const float t = whole + y;
+        comp = (t - whole) - y;
+        whole = t;
+    }
+    float tail = 0.f;
+    for (int q = (qe & ~15); q < qe; ++q) tail += s_y[q];
+    float B = whole + tail;
+    for (int k = 0; k < kNmaxPer; ++k) {
+        const int64_t i = t0 + p0 + k;
+        if (i + nmax <= a.n_samp) acc.add1(B);
+        B = (B - s_y[p0 + k]) + s_y[p0 + k + nmax];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc.merge_down(off);
+    __shared__ float4 s_w[kMsdThreads / 32];
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) s_w[warp] = make_float4(acc.m, acc.Th, acc.Tl, acc.S);
+    __syncthreads();
+    if (warp == 0) {
+        Acc b;
+        if (lane < kMsdThreads / 32) {
+            const float4 v = s_w[lane];
+            b.m = v.x; b.Th = v.y; b.Tl = v.z; b.S = v.w;
+        }
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) b.merge_down(off);
+        if (lane == 0) {
+            MsdPart out;
+            out.n = (double)b.m;
+            out.T = (double)b.Th + (double)b.Tl;
+            out.S = (double)b.S;
+            out.lo = out.hi = 0.0;
+            a.parts[blockIdx.x] = out;
+        }
+    }
+}
+
+__device__ void write_nmax(spd_msd_stats *o, const MsdPart &p, int nmax) {
+    o->nmax = nmax;
+    o->sd_nmax = p.n > 0.0 ? sqrt(p.S / p.n) : 0.0;
+}
+
+__global__ void __launch_bounds__(kMsdThreads) nmax_merge_final_kernel(const MsdPart *scratch,
+                                                                       int n, int nmax,
+                                                                       spd_msd_stats *out) {
+    const MsdPart r = block_merge(scratch, 0, n);
+    if (threadIdx.x == 0) write_nmax(out, r, nmax);
+}
+
+__global__ void __launch_bounds__(kMsdThreads) nmax_merge_rows_kernel(const MsdPart *parts,
+                                                                      int64_t n_dm, int64_t tpr,
+                                                                      int nmax, spd_msd_stats *out) {
+    const int64_t r = blockIdx.x * (int64_t)kMsdThreads + threadIdx.x;
+    if (r >= n_dm) return;
+    MsdPart acc{0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t u = 0; u < tpr; ++u) dmerge(acc, parts[r * tpr + u]);
+    write_nmax(out + r, acc, nmax);
+}
+
 }  // namespace
 
 cudaError_t launch_msd_partial(const MsdArgs &a, int dtype, cudaStream_t s) {
@@ -337,6 +450,36 @@ cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t upr, in
     const int64_t per = (n_parts + n1 - 1) / n1;
     msd_merge_l1_kernel<<<(unsigned)n1, kMsdThreads, 0, s>>>(parts, n_parts, per, scratch);
     msd_merge_final_kernel<<<1, kMsdThreads, 0, s>>>(scratch, (int)n1, out);
+    return cudaGetLastError();
+}
+
+int nmax_blocks(int nmax) { return (kNmaxTile + nmax + 15) / 16 + 1; }
+int64_t nmax_tiles_per_row(int64_t n_samp) { return (n_samp + kNmaxTile - 1) / kNmaxTile; }
+
+cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
+                        spd_msd_stats *out, cudaStream_t s) {
+    const int64_t tiles = a.n_dm * a.tiles_per_row;
+    if (tiles > 0) {
+        const size_t smem = (size_t)a.nb * 17 * sizeof(float);
+        switch (dtype) {
+            case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+            case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+            default: nmax_partial_kernel<SPD_BF16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (a.per_row) {
+        const unsigned g = (unsigned)((a.n_dm + kMsdThreads - 1) / kMsdThreads);
+        nmax_merge_rows_kernel<<<g, kMsdThreads, 0, s>>>(a.parts, a.n_dm, a.tiles_per_row, a.nmax, out);
+        return cudaGetLastError();
+    }
+    int64_t n1 = (tiles + kMsdThreads - 1) / kMsdThreads;
+    if (n1 > n_scratch) n1 = n_scratch;
+    if (n1 < 1) n1 = 1;
+    const int64_t per = (tiles + n1 - 1) / n1;
+    msd_merge_l1_kernel<<<(unsigned)n1, kMsdThreads, 0, s>>>(a.parts, tiles, per, scratch);
+    nmax_merge_final_kernel<<<1, kMsdThreads, 0, s>>>(scratch, (int)n1, a.nmax, out);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,18 @@ def inject_tophat(plane: torch.Tensor, dm: int, t0: int, width: int, amp: float,
     plane[dm, t0:t1] += amp
 
 
+def inject_pulse_train(plane: torch.Tensor, row: int, t0: int, n_pulses: int, width: int,
+                       period: int, amp: float, n_samp: int | None = None):
+    """A train of n_pulses top-hats of `width` samples every `period` samples
+    starting at t0 on one row (signal-dominated rows of the precision form)."""
+    n_samp = plane.shape[1] if n_samp is None else n_samp
+    for k in range(n_pulses):
+        a = t0 + k * period
+        if a >= n_samp:
+            break
+        plane[row, a:min(n_samp, a + width)] += amp
+
+
 def _gauss_profile(fwhm: float, device):
     s = fwhm / 2.3548
     half = int(math.ceil(4.0 * s)) + 1

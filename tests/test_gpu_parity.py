@@ -32,29 +32,36 @@ def _oracle_plane(x, n_samp, scale=None, offset=None):
                         offset=None if offset is None else offset.cpu().numpy())
 
 
-def _full_case(spd, x, n_samp, widths, thr, scope=0, scale=None, offset=None, capacity=None):
+def _full_case(spd, x, n_samp, widths, thr, scope=0, scale=None, offset=None, capacity=None,
+               mode=0, nmax=0):
     """Run every GPU call on x and compare each with the oracle."""
     op = _oracle_plane(x, n_samp, scale, offset)
-    mean, sd, _, tab = oracle.msd_and_sigma(op, widths, oracle.SIGMA_SQRTN, scope)
+    mean, sd, sdn, tab = oracle.msd_and_sigma(op, widths, mode, scope, nmax)
     kw = dict(n_samp=n_samp, scale=scale, offset=offset)
+    nm = int(nmax or widths[-1]) if mode else 0
 
-    m = spd.msd(x, scope, **kw)
+    m = spd.msd(x, scope, nm, **kw)
     torch.cuda.synchronize()
-    P.check_msd(spd.msd_to_numpy(m), mean, sd)
+    gm = spd.msd_to_numpy(m)
+    P.check_msd(gm, mean, sd)
+    if mode:
+        assert np.all(gm["nmax"] == nm)
+        assert np.allclose(gm["sd_nmax"], sdn, rtol=1e-5), (gm["sd_nmax"], sdn)
 
     best_o, win_o = oracle.boxcar_snr(op, mean, sd, tab, widths, scope)
-    snr_g, w_g = spd.boxcar_snr(x, m, widths, spd.SIGMA_SQRTN, scope, **kw)
+    snr_g, w_g = spd.boxcar_snr(x, m, widths, mode, scope, **kw)
     torch.cuda.synchronize()
 
     def sigma_of(e, w):
-        return float(np.atleast_1d(sd)[e] * math.sqrt(w))
+        return float(oracle.sigma_table(mode, float(np.atleast_1d(sd)[e]), [w],
+                                        float(np.atleast_1d(sdn)[e]), nm)[0])
 
     P.check_plane(snr_g.cpu().numpy(), spd.widths_to_numpy(w_g), best_o, win_o, op, mean,
                   sigma_of, scope=scope)
 
     n_o = int((best_o >= thr).sum())
     cap = capacity if capacity is not None else max(n_o + 64, 16)
-    out, res, _ = spd.search(x, widths, thr, cap, spd.SIGMA_SQRTN, scope, **kw)
+    out, res, _ = spd.search(x, widths, thr, cap, mode, scope, nm, **kw)
     count, status = spd.read_result(res)
     assert status == 0
     recs = spd.candidates_to_numpy(out, count)
@@ -204,3 +211,37 @@ def test_figure1_tophat_response(spd):
         m = spd.msd(x)
         snr, w = spd.boxcar_snr(x, m, list(range(1, 65)))
         assert int(spd.widths_to_numpy(w)[0, 1000]) in (W, W + 1, W - 1 if W > 1 else 1)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("scope", [0, 1])
+def test_eq5_linear_sigma(spd, mode, scope):
+    """Eq. 5 (as printed, and read as a linear excess) with sigma_Nmax measured
+    on the GPU, on data with signal-dominated rows (a pulse train)."""
+    sp = synth.ska_like(6, 30000, n_pulses=4, device=DEV, seed=40 + mode)
+    synth.inject_pulse_train(sp.data, row=2, t0=1000, n_pulses=60, width=8, period=32,
+                             amp=6.0 * 12.0, n_samp=sp.n_samp)
+    widths = list(range(1, 17)) + list(range(24, 129, 8))
+    _full_case(spd, sp.data, sp.n_samp, widths, 5.0, scope=scope, mode=mode, nmax=128)
+
+
+@pytest.mark.parametrize("nmax", [2, 17, 256])
+def test_sigma_nmax_against_oracle(spd, nmax):
+    sp = synth.ska_like(5, 20001, n_pulses=3, device=DEV, seed=nmax)
+    op = _oracle_plane(sp.data, sp.n_samp)
+    for scope in (0, 1):
+        want = oracle.plane_sd_nmax(op, nmax, scope)
+        got = spd.msd_to_numpy(spd.msd(sp.data, scope, nmax))
+        assert np.allclose(got["sd_nmax"], want, rtol=1e-5), (got["sd_nmax"], want)
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_precision_form_eq5(spd, dt):
+    """The precision form: FP16 / BF16 storage with per-row scale, 5% of rows
+    signal-dominated, Eq. 5 with sigma_Nmax at Nmax = 256."""
+    sp = synth.ska_like(20, 40000, n_pulses=6, device=DEV, seed=77)
+    synth.inject_pulse_train(sp.data, row=3, t0=2000, n_pulses=125, width=8, period=32,
+                             amp=200 * 12.0 / math.sqrt(1000), n_samp=sp.n_samp)
+    q = synth.quantise_rows(sp, dt)
+    widths = list(range(1, 17)) + list(range(24, 257, 8))
+    _full_case(spd, q.data, q.n_samp, widths, 7.0, scale=q.scale, mode=2, nmax=256)
