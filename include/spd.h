@@ -238,6 +238,56 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
                       spd_msd_stats *msd_out_dev, void *workspace, size_t workspace_bytes,
                       void *stream);
 
+/* One DM range of a batched search: a plane with its own search parameters.
+ * dm_offset is added to the row index in the range's candidate records, so
+ * that ranges can share one record list; decimation records the time
+ * decimation the caller applied to this range (sample and width are in
+ * decimated samples; it does not change the search). */
+typedef struct {
+    spd_plane plane;
+    spd_search_params params;
+    int32_t dm_offset;
+    int32_t decimation;
+} spd_range;
+
+/* Launch shape of the detect kernel (what the autotuner chooses).
+ * ctas_per_sm: persistent CTAs per SM, 0 = as many as fit.
+ * group_scale: widths per group are 16 (step 1) or 2 (16/G + 1) (step G)
+ *   times this factor (>= 1): larger groups mean fewer bounds and group starts,
+ *   smaller groups a finer pruning of the candidate search. */
+typedef struct {
+    int32_t ctas_per_sm;
+    int32_t group_scale;
+    int32_t reserved0;
+    int32_t reserved1;
+} spd_tuning;
+
+#define SPD_MAX_RANGES 8
+
+/* Bytes of device workspace spd_search_batched needs. */
+size_t spd_search_batched_workspace_bytes(const spd_range *ranges, int32_t n_ranges,
+                                          const spd_tuning *tuning);
+
+/* The whole path over up to SPD_MAX_RANGES DM ranges of uneven length, width
+ * set and decimation: per range the MSD (a) and its constants, then ONE
+ * persistent detect launch (b, c, d) whose CTAs walk the tiles of all ranges
+ * -- per launch, ranges whose width lists step by the same G (8, 16 or 1);
+ * ranges must share the storage type.  Every call is a fixed sequence of
+ * asynchronous launches with no host synchronisation and no allocation, so it
+ * can be captured in a CUDA graph and replayed.
+ *   tuning: NULL for the defaults.
+ *   out / capacity / result_dev: one record list for all ranges (records carry
+ *     dm_offset + row).
+ *   msd_out_dev: optional; the ranges' spd_msd_stats concatenated in order
+ *     (1 or n_dm entries each); NULL keeps them in the workspace.
+ * Each range's records are the records spd_search gives for that range alone
+ * (with dm_offset added).  Errors: as spd_search; SPD_ERR_INVALID_ARG for
+ * n_ranges outside 1..SPD_MAX_RANGES or mixed storage types. */
+spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
+                              const spd_tuning *tuning, spd_candidate *out, int64_t capacity,
+                              spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
 /* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
  * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */
 spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out,

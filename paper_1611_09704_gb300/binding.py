@@ -57,6 +57,16 @@ class SpdSearchParams(ctypes.Structure):
                 ("reserved0", ctypes.c_int32)]
 
 
+class SpdRange(ctypes.Structure):
+    _fields_ = [("plane", SpdPlane), ("params", SpdSearchParams), ("dm_offset", ctypes.c_int32),
+                ("decimation", ctypes.c_int32)]
+
+
+class SpdTuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("group_scale", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+
 MSD_BYTES = ctypes.sizeof(SpdMsdStats)      # 40
 CAND_BYTES = ctypes.sizeof(SpdCandidate)    # 16
 RESULT_BYTES = ctypes.sizeof(SpdResult)     # 16
@@ -70,7 +80,7 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_workspace_bytes", "spd_msd", "spd_boxcar_snr_workspace_bytes",
            "spd_boxcar_snr", "spd_threshold_candidates", "spd_detect_workspace_bytes",
            "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums",
-           "spd_msd_noalloc"]
+           "spd_msd_noalloc", "spd_search_batched_workspace_bytes", "spd_search_batched"]
 
 
 class SpdError(RuntimeError):
@@ -129,6 +139,12 @@ def load(path: str | None = None):
     lib.spd_search.restype = I32
     lib.spd_boxcar_sums.argtypes = [pp, I32, P, I64, P]
     lib.spd_boxcar_sums.restype = I32
+    pr = ctypes.POINTER(SpdRange)
+    pt = ctypes.POINTER(SpdTuning)
+    lib.spd_search_batched_workspace_bytes.argtypes = [pr, I32, pt]
+    lib.spd_search_batched_workspace_bytes.restype = SZ
+    lib.spd_search_batched.argtypes = [pr, I32, pt, P, I64, P, P, P, SZ, P]
+    lib.spd_search_batched.restype = I32
     _lib = lib
     return lib
 
@@ -328,6 +344,117 @@ def boxcar_sums(x, w, *, stream=None, out=None, **kw):
     _check(lib.spd_boxcar_sums(ctypes.byref(cp), int(w), _ptr(out), out.stride(0),
                                _stream(stream)), "spd_boxcar_sums")
     return out
+
+
+# ------------------------------------------------------------------ batched
+
+@dataclass
+class RangeSpec:
+    """One DM range of a batched search (see spd_range in include/spd.h)."""
+    x: object                       # torch tensor or Plane
+    widths: list
+    threshold: float
+    sigma_mode: int = SIGMA_SQRTN
+    scope: int = MSD_GLOBAL
+    nmax: int = 0
+    dm_offset: int = 0
+    decimation: int = 1
+
+
+class _Ranges:
+    """ctypes array of spd_range built from RangeSpecs (keeps the width arrays alive)."""
+
+    def __init__(self, specs):
+        self.specs = list(specs)
+        self.planes = [as_plane(r.x) for r in self.specs]
+        self.keep = []
+        arr = (SpdRange * len(self.specs))()
+        for i, (r, pl) in enumerate(zip(self.specs, self.planes)):
+            prm, w = _params(r.widths, r.threshold, r.sigma_mode, r.scope, r.nmax)
+            self.keep.append(w)
+            arr[i] = SpdRange(pl.c(), prm, int(r.dm_offset), int(r.decimation))
+        self.arr = arr
+
+    def n_entries(self):
+        return sum(entries(pl, r.scope) for r, pl in zip(self.specs, self.planes))
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, SpdTuning):
+        return t
+    return SpdTuning(int(t.get("ctas_per_sm", 0)), int(t.get("group_scale", 1)), 0, 0)
+
+
+def search_batched_workspace_bytes(specs, tuning=None) -> int:
+    lib = load()
+    rg = specs if isinstance(specs, _Ranges) else _Ranges(specs)
+    t = _tuning(tuning)
+    return int(lib.spd_search_batched_workspace_bytes(rg.arr, len(rg.specs),
+                                                      ctypes.byref(t) if t else None))
+
+
+def search_batched(specs, capacity, tuning=None, *, stream=None, out=None, result=None,
+                   msd_out=None, workspace=None):
+    """spd_search_batched: (records int32 [capacity, 4], result, msd of every range)."""
+    lib = load()
+    rg = specs if isinstance(specs, _Ranges) else _Ranges(specs)
+    dev = rg.planes[0].data.device
+    t = _tuning(tuning)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 4), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    if msd_out is None:
+        msd_out = torch.empty(max(rg.n_entries(), 1) * MSD_BYTES, dtype=torch.uint8, device=dev)
+    wsb = lib.spd_search_batched_workspace_bytes(rg.arr, len(rg.specs),
+                                                 ctypes.byref(t) if t else None)
+    ws = workspace if workspace is not None else _workspace(wsb, dev)
+    _check(lib.spd_search_batched(rg.arr, len(rg.specs), ctypes.byref(t) if t else None,
+                                  _ptr(out), int(capacity), _ptr(result), _ptr(msd_out),
+                                  _ptr(ws), wsb, _stream(stream)), "spd_search_batched")
+    return out, result, msd_out
+
+
+class BatchedSearch:
+    """A batched search with every buffer allocated once; with graph=True the
+    whole call (MSD launches, constants, the persistent detect launch) is
+    captured in a CUDA graph and replayed by run()."""
+
+    def __init__(self, specs, capacity, tuning=None, graph=True):
+        self.ranges = _Ranges(specs)
+        self.capacity = int(capacity)
+        self.tuning = _tuning(tuning)
+        dev = self.ranges.planes[0].data.device
+        self.out = torch.empty((max(self.capacity, 1), 4), dtype=torch.int32, device=dev)
+        self.result = torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=dev)
+        self.msd = torch.empty(max(self.ranges.n_entries(), 1) * MSD_BYTES, dtype=torch.uint8,
+                               device=dev)
+        wsb = search_batched_workspace_bytes(self.ranges, self.tuning)
+        self.ws = _workspace(wsb, dev)
+        self.graph = None
+        if graph:
+            s = torch.cuda.Stream(device=dev)
+            s.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(s):
+                self._call(s)          # warm-up outside capture (attributes, lazy loading)
+            torch.cuda.current_stream(dev).wait_stream(s)
+            torch.cuda.synchronize(dev)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._call(None)
+
+    def _call(self, stream):
+        search_batched(self.ranges, self.capacity, self.tuning, stream=stream, out=self.out,
+                       result=self.result, msd_out=self.msd, workspace=self.ws)
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._call(None)
+        return self.out, self.result
 
 
 # ------------------------------------------------------------------ decoding

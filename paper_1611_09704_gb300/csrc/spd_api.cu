@@ -87,11 +87,11 @@ MsdLayout msd_layout(const spd_plane *p, int nmax = 0) {
 // Evaluated widths are width 1 (the starting value of Algorithm 1) followed
 // by the listed widths.  They are cut into groups of consecutive widths that
 // step by 1 (the running sum adds one sample per width) or by G (it adds one
-// G-sample window sum); a group's sums start from the prefix sums at `off`.
-// Groups hold at most 16 (step 1) or 2 (16/G + 1) (step G) widths, doubled
-// until there are at most 64 groups, and never cross a multiple of 64 in eval
-// index.  G is the most frequent step of 8 or 16, if any.
-spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
+// G-sample window sum); a group's sums start from the block sums at `off`.
+// Groups hold at most 16 (step 1) or 2 (16/G + 1) (step G) widths times
+// `scale`, doubled until there are at most 64 groups, and never cross a
+// multiple of 64 in eval index.  G is the most frequent step of 8 or 16, if any.
+spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, int scale0 = 1) {
     if (!widths || n < 1 || n > SPD_MAX_WIDTHS) return SPD_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k) {
         if (widths[k] < 1 || widths[k] > SPD_MAX_WIDTH) return SPD_ERR_INVALID_ARG;
@@ -110,7 +110,7 @@ spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
     const int G = (n8 || n16) ? (n8 >= n16 ? 8 : 16) : 0;
 
     std::vector<Group> groups;
-    for (int scale = 1;; scale *= 2) {
+    for (int scale = scale0 < 1 ? 1 : scale0;; scale *= 2) {
         const int max_fine = 16 * scale, max_coarse = (G ? 2 * (16 / G + 1) : 1) * scale;
         groups.clear();
         for (int k = 0; k < ne; ++k) {
@@ -143,27 +143,24 @@ spd_status compile_program(const int32_t *widths, int32_t n, Program &prog) {
     prog.wmax = E.back();
     prog.G = G;
     for (size_t i = 0; i < groups.size(); ++i) prog.groups[i] = groups[i];
-    for (int k = 0; k < ne; ++k) prog.eval_w[k] = (uint16_t)E[k];
     return SPD_OK;
 }
 
 // Blocks of 16 positions staged per tile: the tile, the halo and slack for
 // window loads that run past the last width.
-int program_R(const Program &prog) { return (kTile + prog.wmax + 32 + 15) / 16 + 1; }
-int program_span(const Program &prog) { return kTile + prog.wmax - 1; }
-int program_raw_bytes(const Program &prog, int dtype) {
-    return (int)((program_span(prog) * elem_bytes(dtype) + 15) / 16 * 16);
-}
+int prog_R(const RangeProg &prog) { return (kTile + prog.wmax + 32 + 15) / 16 + 1; }
+int prog_span(const RangeProg &prog) { return kTile + prog.wmax - 1; }
+int raw_bytes_of(int span, int dtype) { return (int)((span * elem_bytes(dtype) + 15) / 16 * 16); }
 
 // Shared memory of one detect CTA: two raw staging buffers, the centred
-// samples and window sums (20 words per 16 positions), per-block prefix data,
-// 1/sigma_w per width and per group.
-size_t program_smem(const Program &prog, int dtype) {
-    const size_t R = program_R(prog);
-    size_t b = 16 + 2 * (size_t)program_raw_bytes(prog, dtype);
-    b += (size_t)(prog.G ? 2 : 1) * 20 * R * sizeof(float);
-    b += R * 3 * sizeof(float);   // block sums, largest and smallest prefix
-    b += ((size_t)prog.n_eval + prog.n_groups) * sizeof(float);
+// samples and window sums (20 words per 16 positions), per-block sums and
+// prefix bounds, 1/sigma_w and the width per eval index, 1/sigma_w per group.
+size_t launch_smem(int R, int raw_bytes, int max_eval, int G) {
+    size_t b = 16 + 2 * (size_t)raw_bytes;
+    b += (size_t)(G ? 2 : 1) * 20 * R * sizeof(float);
+    b += (size_t)R * 3 * sizeof(float);
+    b += (size_t)max_eval * sizeof(float) + kMaxCodeGroups * sizeof(float);
+    b += (size_t)max_eval * sizeof(uint16_t);
     return (b + 15) / 16 * 16;
 }
 
@@ -207,54 +204,85 @@ int nmax_of(const spd_search_params *q) {
     return q->widths && q->n_widths > 0 ? q->widths[q->n_widths - 1] : 0;
 }
 
-// Constants + one detect launch (plane output or candidates).
-spd_status run_detect(const spd_plane *p, const Program &prog, const spd_msd_stats *msd_dev,
-                      int scope, int sigma_mode, float thr, spd_candidate *out, int64_t cap,
-                      spd_result *result, float *snr_out, uint16_t *width_out,
-                      int64_t out_stride, void *ws, cudaStream_t st) {
+// Constants kernel for one range: 1/sigma_w per entry and width, mean, flags.
+spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd_stats *msd_dev,
+                        int scope, int sigma_mode, spd_result *result, void *ws,
+                        cudaStream_t st, RangeDesc &rd) {
     const int64_t entries = entries_of(p, scope);
     const DetLayout L = det_layout(entries, prog.n_eval);
     char *base = static_cast<char *>(ws);
-    float *inv = reinterpret_cast<float *>(base + L.inv_off);
-    float2 *mu = reinterpret_cast<float2 *>(base + L.mu_off);
-    int32_t *flags = reinterpret_cast<int32_t *>(base + L.flags_off);
-
     ConstArgs c;
     c.msd = msd_dev;
     c.entries = (int)entries;
     c.sigma_mode = sigma_mode;
-    c.inv_tab = inv;
-    c.mu_tab = mu;
-    c.flags = flags;
+    c.inv_tab = reinterpret_cast<float *>(base + L.inv_off);
+    c.mu_tab = reinterpret_cast<float2 *>(base + L.mu_off);
+    c.flags = reinterpret_cast<int32_t *>(base + L.flags_off);
     c.result = result;
     SPD_CK(launch_consts(c, prog, st));
 
-    DetectArgs a;
-    memset(&a, 0, sizeof(a));
-    a.data = p->data;
-    a.n_dm = p->n_dm;
-    a.n_samp = p->n_samp;
-    a.stride = p->row_stride;
-    a.scale = p->row_scale;
-    a.offset = p->row_offset;
-    a.vec_ok = plane_vec_ok(p);
-    a.per_row = scope == SPD_MSD_PER_ROW;
-    a.inv_tab = inv;
-    a.mu_tab = mu;
-    a.flags = flags;
-    a.R = program_R(prog);
-    a.span = program_span(prog);
-    a.raw_bytes = program_raw_bytes(prog, p->dtype);
-    a.tiles_per_row = (p->n_samp + kTile - 1) / kTile;
-    a.threshold = thr;
-    a.out = out;
-    a.capacity = cap;
-    a.result = result;
-    a.snr_out = snr_out;
-    a.width_out = width_out;
-    a.out_stride = out_stride;
-    SPD_CK(launch_detect(a, prog, p->dtype, snr_out != nullptr, program_smem(prog, p->dtype), st));
+    memset(&rd, 0, sizeof(rd));
+    rd.data = p->data;
+    rd.n_dm = p->n_dm;
+    rd.n_samp = p->n_samp;
+    rd.stride = p->row_stride;
+    rd.scale = p->row_scale;
+    rd.offset = p->row_offset;
+    rd.inv_tab = c.inv_tab;
+    rd.mu_tab = c.mu_tab;
+    rd.flags = c.flags;
+    rd.tiles_per_row = (p->n_samp + kTile - 1) / kTile;
+    rd.vec_ok = plane_vec_ok(p);
+    rd.per_row = scope == SPD_MSD_PER_ROW;
+    rd.R = prog_R(prog);
+    rd.span = prog_span(prog);
+    rd.prog = prog;
     return SPD_OK;
+}
+
+// One detect launch over ranges rd[0 .. n) (same storage type and G).
+spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out, int64_t cap,
+                      spd_result *result, float *snr_out, uint16_t *width_out,
+                      int64_t out_stride, int ctas_per_sm, cudaStream_t st) {
+    static thread_local Launch L;
+    memset(&L, 0, sizeof(L));
+    int64_t tiles = 0;
+    int R = 0, raw = 0, max_eval = 0, G = rd[0].prog.G;
+    for (int i = 0; i < n; ++i) {
+        L.rng[i] = rd[i];
+        L.rng[i].tile0 = tiles;
+        tiles += rd[i].n_dm * rd[i].tiles_per_row;
+        R = rd[i].R > R ? rd[i].R : R;
+        const int rb = raw_bytes_of(rd[i].span, dtype);
+        raw = rb > raw ? rb : raw;
+        max_eval = rd[i].prog.n_eval > max_eval ? rd[i].prog.n_eval : max_eval;
+    }
+    L.n_ranges = n;
+    L.R = R;
+    L.raw_bytes = raw;
+    L.max_eval = max_eval;
+    L.n_tiles = tiles;
+    L.out = out;
+    L.capacity = cap;
+    L.result = result;
+    L.snr_out = snr_out;
+    L.width_out = width_out;
+    L.out_stride = out_stride;
+    const size_t smem = launch_smem(R, raw, max_eval, G);
+    if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
+    SPD_CK(launch_detect(L, dtype, G, snr_out != nullptr, max_eval > 64, smem, ctas_per_sm, st));
+    return SPD_OK;
+}
+
+// Constants + one detect launch over one plane (plane output or candidates).
+spd_status run_detect(const spd_plane *p, const RangeProg &prog, const spd_msd_stats *msd_dev,
+                      int scope, int sigma_mode, float thr, spd_candidate *out, int64_t cap,
+                      spd_result *result, float *snr_out, uint16_t *width_out,
+                      int64_t out_stride, void *ws, cudaStream_t st) {
+    RangeDesc rd;
+    SPD_TRY(range_consts(p, prog, msd_dev, scope, sigma_mode, result, ws, st, rd));
+    rd.threshold = thr;
+    return run_launch(&rd, 1, p->dtype, out, cap, result, snr_out, width_out, out_stride, 0, st);
 }
 
 }  // namespace
@@ -341,7 +369,7 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
 size_t spd_boxcar_snr_workspace_bytes(const spd_plane *plane, int32_t scope,
                                       const int32_t *widths, int32_t n_widths) {
     if (check_plane(plane) != SPD_OK || !scope_ok(scope)) return 0;
-    Program prog;
+    RangeProg prog;
     if (compile_program(widths, n_widths, prog) != SPD_OK) return 0;
     return det_layout(entries_of(plane, scope), prog.n_eval).total;
 }
@@ -354,7 +382,7 @@ spd_status spd_boxcar_snr(const spd_plane *plane, const spd_msd_stats *msd_dev, 
     if (!scope_ok(scope)) return SPD_ERR_INVALID_ARG;
     if (sigma_mode < SPD_SIGMA_SQRTN || sigma_mode > SPD_SIGMA_LINEAR_EXCESS)
         return SPD_ERR_INVALID_ARG;
-    static thread_local Program prog;
+    static thread_local RangeProg prog;
     SPD_TRY(compile_program(widths, n_widths, prog));
     if (plane_empty(plane)) return SPD_OK;
     if (!msd_dev || !snr_out || !width_out || out_stride < plane->n_samp)
@@ -387,7 +415,7 @@ spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int
 
 size_t spd_detect_workspace_bytes(const spd_plane *plane, const spd_search_params *params) {
     if (check_plane(plane) != SPD_OK || check_params(params) != SPD_OK) return 0;
-    Program prog;
+    RangeProg prog;
     if (compile_program(params->widths, params->n_widths, prog) != SPD_OK) return 0;
     return det_layout(entries_of(plane, params->msd_scope), prog.n_eval).total;
 }
@@ -398,7 +426,7 @@ spd_status spd_detect(const spd_plane *plane, const spd_search_params *params,
                       void *stream) {
     SPD_TRY(check_plane(plane));
     SPD_TRY(check_params(params));
-    static thread_local Program prog;
+    static thread_local RangeProg prog;
     SPD_TRY(compile_program(params->widths, params->n_widths, prog));
     if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
     if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
@@ -418,7 +446,7 @@ spd_status spd_detect(const spd_plane *plane, const spd_search_params *params,
 
 size_t spd_search_workspace_bytes(const spd_plane *plane, const spd_search_params *params) {
     if (check_plane(plane) != SPD_OK || check_params(params) != SPD_OK) return 0;
-    Program prog;
+    RangeProg prog;
     if (compile_program(params->widths, params->n_widths, prog) != SPD_OK) return 0;
     const int64_t entries = entries_of(plane, params->msd_scope);
     return msd_layout(plane, nmax_of(params)).total +
@@ -431,7 +459,7 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
                       void *stream) {
     SPD_TRY(check_plane(plane));
     SPD_TRY(check_params(params));
-    static thread_local Program prog;
+    static thread_local RangeProg prog;
     SPD_TRY(compile_program(params->widths, params->n_widths, prog));
     if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
     if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
@@ -452,6 +480,107 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
     return run_detect(plane, prog, msd, params->msd_scope, params->sigma_mode,
                       params->threshold, out, capacity, result_dev, nullptr, nullptr, 0,
                       base + ML.total + msd_bytes, st);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct BatchLayout {
+    size_t msd_off[kMaxRanges], stats_off[kMaxRanges], det_off[kMaxRanges], total;
+    size_t msd_bytes[kMaxRanges];
+};
+
+spd_status batch_plan(const spd_range *ranges, int n, const spd_tuning *tuning,
+                      RangeProg *progs, BatchLayout &L) {
+    if (!ranges || n < 1 || n > kMaxRanges) return SPD_ERR_INVALID_ARG;
+    const int scale = tuning && tuning->group_scale > 0 ? tuning->group_scale : 1;
+    if (tuning && (tuning->ctas_per_sm < 0 || tuning->group_scale < 0)) return SPD_ERR_INVALID_ARG;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const spd_range &r = ranges[i];
+        SPD_TRY(check_plane(&r.plane));
+        SPD_TRY(check_params(&r.params));
+        if (r.plane.dtype != ranges[0].plane.dtype) return SPD_ERR_INVALID_ARG;
+        if (r.dm_offset < 0 || r.decimation < 0) return SPD_ERR_INVALID_ARG;
+        SPD_TRY(compile_program(r.params.widths, r.params.n_widths, progs[i], scale));
+        const int64_t entries = entries_of(&r.plane, r.params.msd_scope);
+        L.msd_off[i] = off;
+        L.msd_bytes[i] = msd_layout(&r.plane, nmax_of(&r.params)).total;
+        off += align_up(L.msd_bytes[i]);
+        L.stats_off[i] = off;
+        off += align_up((size_t)entries * sizeof(spd_msd_stats));
+        L.det_off[i] = off;
+        off += align_up(det_layout(entries, progs[i].n_eval).total);
+    }
+    L.total = off;
+    return SPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t spd_search_batched_workspace_bytes(const spd_range *ranges, int32_t n_ranges,
+                                          const spd_tuning *tuning) {
+    RangeProg progs[kMaxRanges];
+    BatchLayout L;
+    if (batch_plan(ranges, n_ranges, tuning, progs, L) != SPD_OK) return 0;
+    return L.total;
+}
+
+spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
+                              const spd_tuning *tuning, spd_candidate *out, int64_t capacity,
+                              spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                              void *workspace, size_t workspace_bytes, void *stream) {
+    static thread_local RangeProg progs[kMaxRanges];
+    BatchLayout L;
+    SPD_TRY(batch_plan(ranges, n_ranges, tuning, progs, L));
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    SPD_TRY(check_ws(workspace, workspace_bytes, L.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+
+    // (a) per range, and the constants of (c)
+    RangeDesc rds[kMaxRanges];
+    int live[kMaxRanges], n_live = 0;
+    int64_t msd_pos = 0;
+    for (int i = 0; i < n_ranges; ++i) {
+        const spd_range &r = ranges[i];
+        const int64_t entries = entries_of(&r.plane, r.params.msd_scope);
+        spd_msd_stats *msd = msd_out_dev ? msd_out_dev + msd_pos
+                                         : reinterpret_cast<spd_msd_stats *>(base + L.stats_off[i]);
+        msd_pos += entries;
+        if (plane_empty(&r.plane)) continue;
+        SPD_TRY(spd_msd(&r.plane, r.params.msd_scope, nmax_of(&r.params), msd,
+                        base + L.msd_off[i], L.msd_bytes[i], stream));
+        SPD_TRY(range_consts(&r.plane, progs[i], msd, r.params.msd_scope, r.params.sigma_mode,
+                             result_dev, base + L.det_off[i], st, rds[i]));
+        rds[i].threshold = r.params.threshold;
+        rds[i].dm_offset = r.dm_offset;
+        live[n_live++] = i;
+    }
+    // (b, c, d): one persistent launch per class of ranges with equal G and
+    // equal bulk-copy eligibility
+    bool done[kMaxRanges] = {false};
+    for (int a = 0; a < n_live; ++a) {
+        const int i = live[a];
+        if (done[i]) continue;
+        RangeDesc grp[kMaxRanges];
+        int m = 0;
+        for (int b = a; b < n_live; ++b) {
+            const int j = live[b];
+            if (done[j] || rds[j].prog.G != rds[i].prog.G || rds[j].vec_ok != rds[i].vec_ok)
+                continue;
+            grp[m++] = rds[j];
+            done[j] = true;
+        }
+        SPD_TRY(run_launch(grp, m, ranges[0].plane.dtype, out, capacity, result_dev, nullptr,
+                           nullptr, 0, tuning ? tuning->ctas_per_sm : 0, st));
+    }
+    return SPD_OK;
 }
 
 spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out, int64_t out_stride,

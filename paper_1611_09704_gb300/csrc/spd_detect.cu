@@ -5,16 +5,16 @@
 namespace spd {
 
 template <int DT>
-cudaError_t launch_detect_dt(const DetectArgs &a, const Program &prog, bool plane_out,
-                             size_t smem, cudaStream_t s);
+cudaError_t launch_detect_dt(const Launch &L, int G, bool plane_out, bool multi_block,
+                             size_t smem, int ctas_per_sm, cudaStream_t s);
 
-cudaError_t launch_detect(const DetectArgs &a, const Program &prog, int dtype, bool plane_out,
-                          size_t smem, cudaStream_t s) {
-    if (a.n_dm * a.tiles_per_row <= 0) return cudaSuccess;
+cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
+                          size_t smem, int ctas_per_sm, cudaStream_t s) {
+    if (L.n_tiles <= 0) return cudaSuccess;
     switch (dtype) {
-        case SPD_F32: return launch_detect_dt<SPD_F32>(a, prog, plane_out, smem, s);
-        case SPD_F16: return launch_detect_dt<SPD_F16>(a, prog, plane_out, smem, s);
-        default: return launch_detect_dt<SPD_BF16>(a, prog, plane_out, smem, s);
+        case SPD_F32: return launch_detect_dt<SPD_F32>(L, G, plane_out, multi_block, smem, ctas_per_sm, s);
+        case SPD_F16: return launch_detect_dt<SPD_F16>(L, G, plane_out, multi_block, smem, ctas_per_sm, s);
+        default: return launch_detect_dt<SPD_BF16>(L, G, plane_out, multi_block, smem, ctas_per_sm, s);
     }
 }
 

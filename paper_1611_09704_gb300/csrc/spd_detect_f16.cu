@@ -3,6 +3,6 @@
 #include "spd_detect_kernel.cuh"
 
 namespace spd {
-template cudaError_t launch_detect_dt<SPD_F16>(const DetectArgs &, const Program &, bool, size_t,
+template cudaError_t launch_detect_dt<SPD_F16>(const Launch &, int, bool, bool, size_t, int,
                                           cudaStream_t);
 }  // namespace spd

@@ -534,42 +534,50 @@ __device__ void build_stats(const float *s_y, float *s_g, float *s_bs, float *s_
     __syncthreads();
 }
 
-// Largest 1/sigma_w of each group (for the bounds of the candidate search).
-__device__ __forceinline__ void group_inv_max(const Program &prog, const float *s_inv,
-                                              float *s_ginv) {
-    for (int gi = threadIdx.x; gi < prog.n_groups; gi += kThreads) {
-        const Group g = prog.groups[gi];
+// Per-range constants in shared memory: 1/sigma_w per eval index, the width
+// of each eval index, and (candidate search) the largest 1/sigma_w per group.
+__device__ __forceinline__ void load_range_consts(const RangeDesc &rd, int entry, float *s_inv,
+                                                  uint16_t *s_ew, float *s_ginv, bool ginv) {
+    const RangeProg &rp = rd.prog;
+    for (int q = threadIdx.x; q < rp.n_eval; q += kThreads)
+        s_inv[q] = rd.inv_tab[(int64_t)entry * rp.n_eval + q];
+    for (int gi = threadIdx.x; gi < rp.n_groups; gi += kThreads) {
+        const Group g = rp.groups[gi];
+        const int d = (g.flags & kGroupCoarse) ? rp.G : 1;
         float mxv = 0.f;
-        for (int c = 0; c < g.count; ++c) mxv = fmaxf(mxv, s_inv[g.widx0 + c]);
-        s_ginv[gi] = mxv;
+        for (int c = 0; c < g.count; ++c) {
+            s_ew[g.widx0 + c] = (uint16_t)(g.off + (c + 1) * d);
+            if (ginv) mxv = fmaxf(mxv, rd.inv_tab[(int64_t)entry * rp.n_eval + g.widx0 + c]);
+        }
+        if (ginv) s_ginv[gi] = mxv;
     }
 }
 
 template <int DT, int G, bool PLANE, bool MG>
-__global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
-                                                             const __grid_constant__ Program prog) {
+__global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_constant__ Launch L) {
     using T = typename Elem<DT>::T;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int R = a.R;
+    const int RM = L.R;
     uint64_t *s_bar = reinterpret_cast<uint64_t *>(smem);
     unsigned char *s_raw0 = smem + 16;
-    float *s_y = reinterpret_cast<float *>(s_raw0 + 2 * a.raw_bytes);
-    float *s_g = s_y + kPad * R;
-    float *s_bs = s_y + (G > 1 ? 2 : 1) * kPad * R;
-    float *s_mx = s_bs + R;
-    float *s_mn = s_mx + R;
-    float *s_inv = s_mn + R;
-    float *s_ginv = s_inv + prog.n_eval;
+    float *s_y = reinterpret_cast<float *>(s_raw0 + 2 * L.raw_bytes);
+    float *s_g = s_y + kPad * RM;
+    float *s_bs = s_y + (G > 1 ? 2 : 1) * kPad * RM;
+    float *s_mx = s_bs + RM;
+    float *s_mn = s_mx + RM;
+    float *s_inv = s_mn + RM;
+    float *s_ginv = s_inv + L.max_eval;
+    uint16_t *s_ew = reinterpret_cast<uint16_t *>(s_ginv + kMaxCodeGroups);
     __shared__ int s_wsum[kThreads / 32];
     __shared__ unsigned long long s_base;
     __shared__ float s_wt[3 * (kThreads / 32) + 3 * kThreads];
 
     const int tid = threadIdx.x;
-    const int64_t n_tiles = a.n_dm * a.tiles_per_row;
-    const int span = a.span;
-    const bool tma = a.vec_ok != 0;
+    const int64_t n_tiles = L.n_tiles;
     const int64_t esz = (int64_t)sizeof(T);
 
+    // all ranges of a launch agree on bulk copies (the host checks)
+    const bool tma = L.rng[0].vec_ok != 0;
     if (tma) {
         if (tid == 0) {
             mbar_init(s_bar);
@@ -578,60 +586,70 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         }
         __syncthreads();
     }
+    auto range_of = [&](int64_t tile, int from) {
+        int r = from;
+        while (r + 1 < L.n_ranges && tile >= L.rng[r + 1].tile0) ++r;
+        return r;
+    };
     // bulk copy of tile `tile`'s window into raw buffer `buf` (thread 0 only)
-    auto issue = [&](int64_t tile, int buf) {
-        const int64_t row = tile / a.tiles_per_row;
-        const int64_t t0 = (tile - row * a.tiles_per_row) * (int64_t)kTile;
-        const int64_t have = min((int64_t)span, a.n_samp - t0);
+    auto issue = [&](int64_t tile, int ri, int buf) {
+        const RangeDesc &rd = L.rng[ri];
+        const int64_t lt = tile - rd.tile0;
+        const int64_t row = lt / rd.tiles_per_row;
+        const int64_t t0 = (lt - row * rd.tiles_per_row) * (int64_t)kTile;
+        const int64_t have = min((int64_t)rd.span, rd.n_samp - t0);
         const uint32_t nb = (uint32_t)((have * esz) & ~(int64_t)15);
         uint64_t *bar = s_bar + buf;
         fence_proxy_async();
         mbar_expect(bar, nb);
         if (nb) {
-            const T *src = static_cast<const T *>(a.data) + row * a.stride + t0;
-            bulk_load(s_raw0 + buf * a.raw_bytes, src, nb, bar);
+            const T *src = static_cast<const T *>(rd.data) + row * rd.stride + t0;
+            bulk_load(s_raw0 + buf * L.raw_bytes, src, nb, bar);
         }
     };
-    if (tma && tid == 0 && (int64_t)blockIdx.x < n_tiles) issue(blockIdx.x, 0);
-    if (!a.per_row) {   // one MSD for the whole plane: constants once per CTA
-        for (int q = tid; q < prog.n_eval; q += kThreads) s_inv[q] = a.inv_tab[q];
-        __syncthreads();
-        if (!PLANE) group_inv_max(prog, s_inv, s_ginv);
-        // visible after the first tile's staging barrier
-    }
+    if (tma && tid == 0 && (int64_t)blockIdx.x < n_tiles)
+        issue(blockIdx.x, range_of(blockIdx.x, 0), 0);
 
-    int k = 0;
+    int k = 0, ri = 0;
+    int64_t key = -1;   // (range, scope entry) whose constants are in shared memory
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
         const int buf = k & 1;
-        const int64_t row = tile / a.tiles_per_row;
-        const int64_t t0 = (tile - row * a.tiles_per_row) * (int64_t)kTile;
-        const int entry = a.per_row ? (int)row : 0;
+        ri = range_of(tile, ri);
+        const RangeDesc &rd = L.rng[ri];
+        const RangeProg &rp = rd.prog;
+        const int R = rd.R;
+        const int64_t lt = tile - rd.tile0;
+        const int64_t row = lt / rd.tiles_per_row;
+        const int64_t t0 = (lt - row * rd.tiles_per_row) * (int64_t)kTile;
+        const int entry = rd.per_row ? (int)row : 0;
         const int64_t i0 = t0 + (int64_t)tid * kX;   // first start sample of this thread
-        const T *rowp = static_cast<const T *>(a.data) + row * a.stride;
+        const T *rowp = static_cast<const T *>(rd.data) + row * rd.stride;
 
         if (tma && !mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1))) {
             // the copy did not land in time: report it, give the copy one more
             // bounded wait, and leave this CTA
             if (tid == 0) {
-                if (a.result) atomicExch(&a.result->status, (int)SPD_ERR_TIMEOUT);
+                if (L.result) atomicExch(&L.result->status, (int)SPD_ERR_TIMEOUT);
                 mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
             }
             return;
         }
 
-        const bool deg = a.flags[entry] != 0;
-        const float2 mu = a.mu_tab[entry];
-        const bool has_sc = a.scale != nullptr;
-        const float sc = has_sc ? a.scale[row] : 1.f;
-        const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
-        const int64_t have = min((int64_t)span, a.n_samp - t0);
+        const bool deg = rd.flags[entry] != 0;
+        const float2 mu = rd.mu_tab[entry];
+        const bool has_sc = rd.scale != nullptr;
+        const float sc = has_sc ? rd.scale[row] : 1.f;
+        const float of = (has_sc && rd.offset) ? rd.offset[row] : 0.f;
+        const int64_t have = min((int64_t)rd.span, rd.n_samp - t0);
         const int nraw = tma ? (int)(((have * esz) & ~(int64_t)15) / esz) : 0;
-        const T *raw = reinterpret_cast<const T *>(s_raw0 + buf * a.raw_bytes);
+        const T *raw = reinterpret_cast<const T *>(s_raw0 + buf * L.raw_bytes);
 
         if (!deg) {
-            if (a.per_row)
-                for (int q = tid; q < prog.n_eval; q += kThreads)
-                    s_inv[q] = a.inv_tab[(int64_t)entry * prog.n_eval + q];
+            const int64_t nk = ((int64_t)ri << 32) | (uint32_t)entry;
+            if (nk != key) {
+                load_range_consts(rd, entry, s_inv, s_ew, s_ginv, !PLANE);
+                key = nk;
+            }
             // Stage centred samples; -inf past the row end and past the window.
             for (int q = tid; q < 4 * R; q += kThreads) {
                 const int p = 4 * q;
@@ -659,14 +677,15 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         }
         __syncthreads();
         // the raw buffer is free again: prefetch the window of the tile after
-        if (tma && tid == 0 && tile + gridDim.x < n_tiles) issue(tile + gridDim.x, buf ^ 1);
+        if (tma && tid == 0 && tile + gridDim.x < n_tiles)
+            issue(tile + gridDim.x, range_of(tile + gridDim.x, ri), buf ^ 1);
 
         if (deg) {
             if (PLANE) {
                 for (int q = 0; q < kX; ++q) {
-                    if (i0 + q < a.n_samp) {
-                        a.snr_out[row * a.out_stride + i0 + q] = __int_as_float(0x7fc00000);
-                        a.width_out[row * a.out_stride + i0 + q] = 0;
+                    if (i0 + q < rd.n_samp) {
+                        L.snr_out[row * L.out_stride + i0 + q] = __int_as_float(0x7fc00000);
+                        L.width_out[row * L.out_stride + i0 + q] = 0;
                     }
                 }
             }
@@ -674,10 +693,6 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         }
 
         build_stats<G>(s_y, s_g, s_bs, s_mx, s_mn, s_wt, R);   // ends with a barrier
-        if (!PLANE && a.per_row) {
-            group_inv_max(prog, s_inv, s_ginv);
-            __syncthreads();
-        }
 
         const float *sy_t = s_y + kPad * tid;
         const float *sg_t = s_g + kPad * tid;
@@ -696,8 +711,8 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
 #pragma unroll
             for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
             int cur = 0;   // block of 64 eval indices being packed
-            for (int gi = 0; gi < prog.n_groups; ++gi) {
-                const Group g = prog.groups[gi];
+            for (int gi = 0; gi < rp.n_groups; ++gi) {
+                const Group g = rp.groups[gi];
                 if (MG && (g.widx0 >> 6) != cur) {
                     // blocks of 64 widths: a later block wins only with a larger
                     // value (its code bits say nothing about earlier blocks)
@@ -728,11 +743,11 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
                 const uint32_t bits = __float_as_uint(bv);
                 const int wi = (MG ? ogrp[q] : 0) * 64 + (63 - (int)(bits & 63u));
                 snr[q] = __uint_as_float(bits & 0xFFFFFFC0u);
-                wdt[q] = (wi < prog.n_eval) ? (int)prog.eval_w[wi] : 0;
+                wdt[q] = (wi < rp.n_eval) ? (int)s_ew[wi] : 0;
             }
-            float *so = a.snr_out + row * a.out_stride;
-            uint16_t *wo = a.width_out + row * a.out_stride;
-            const bool full = i0 + kX <= a.n_samp;
+            float *so = L.snr_out + row * L.out_stride;
+            uint16_t *wo = L.width_out + row * L.out_stride;
+            const bool full = i0 + kX <= rd.n_samp;
             const bool al = ((reinterpret_cast<uintptr_t>(so + i0) & 15) == 0) &&
                             ((reinterpret_cast<uintptr_t>(wo + i0) & 15) == 0);
             if (full && al) {
@@ -752,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
             } else {
 #pragma unroll
                 for (int q = 0; q < kX; ++q) {
-                    if (i0 + q < a.n_samp) {
+                    if (i0 + q < rd.n_samp) {
                         so[i0 + q] = snr[q];
                         wo[i0 + q] = (uint16_t)wdt[q];
                     }
@@ -763,7 +778,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         }
 
         // ------------------------------------------------ candidate search
-        const float thr = a.threshold;
+        const float thr = rd.threshold;
         const float minC = s_mn[tid];
         FindSink fk;
         float *best = fk.best;
@@ -771,8 +786,8 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
         MaxSink mk;
         float minbest = -INFINITY;   // smallest current best of the 16 samples
-        for (int gi = prog.n_groups - 1; gi >= 0; --gi) {
-            const Group g = prog.groups[gi];
+        for (int gi = rp.n_groups - 1; gi >= 0; --gi) {
+            const Group g = rp.groups[gi];
             const int d = group_step<G>(g);
             // upper bound over the thread's 16 samples and the group's widths
             const int jb0 = tid + ((g.off + d) >> 4);
@@ -802,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
 #pragma unroll
         for (int q = 0; q < kX; ++q) {
             fk.found[q] = -1;
-            if (i0 + q < a.n_samp && trunc17(best[q]) >= thr) {
+            if (i0 + q < rd.n_samp && trunc17(best[q]) >= thr) {
                 mask |= 1u << q;
                 need |= 1ull << (63u - (__float_as_uint(best[q]) & 63u));
             }
@@ -811,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
         while (need) {
             const int gi = __ffsll((long long)need) - 1;
             need &= need - 1;
-            const Group g = prog.groups[gi];
+            const Group g = rp.groups[gi];
             fk.code = 63u - (uint32_t)gi;
             group_start(B, s_y, s_bs, tid, g.off);
             run_group_compact<G>(B, fk, sy_t, sg_t, g, s_inv);
@@ -819,7 +834,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
 #pragma unroll
         for (int q = 0; q < kX; ++q) {
             snr[q] = trunc17(best[q]);
-            wdt[q] = fk.found[q] >= 0 ? (int)prog.eval_w[fk.found[q]] : 0;
+            wdt[q] = fk.found[q] >= 0 ? (int)s_ew[fk.found[q]] : 0;
         }
 
         // Threshold (Sec. 2.4, inclusive) and block-aggregated compaction.
@@ -844,7 +859,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
             if (lane < kThreads / 32) s_wsum[lane] = wsc - wv;   // exclusive
             const int total = __shfl_sync(0xffffffffu, wsc, kThreads / 32 - 1);
             if (lane == 0)
-                s_base = total ? atomicAdd(reinterpret_cast<unsigned long long *>(&a.result->count),
+                s_base = total ? atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
                                            (unsigned long long)total)
                                : 0ull;
         }
@@ -854,13 +869,13 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
 #pragma unroll
             for (int q = 0; q < kX; ++q) {
                 if (mask & (1u << q)) {
-                    if (idx < (unsigned long long)a.capacity) {
+                    if (idx < (unsigned long long)L.capacity) {
                         int4 rec;
-                        rec.x = (int)row;
+                        rec.x = rd.dm_offset + (int)row;
                         rec.y = (int)(i0 + q);
                         rec.z = __float_as_int(snr[q]);
                         rec.w = wdt[q];
-                        reinterpret_cast<int4 *>(a.out)[idx] = rec;
+                        reinterpret_cast<int4 *>(L.out)[idx] = rec;
                     }
                     ++idx;
                 }
@@ -872,15 +887,14 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const DetectArgs a,
 }
 
 template <int DT, int G>
-cudaError_t launch_dg(const DetectArgs &a, const Program &prog, bool plane_out, bool mg,
-                      size_t smem, cudaStream_t s) {
-    const int64_t tiles = a.n_dm * a.tiles_per_row;
+cudaError_t launch_dg(const Launch &L, bool plane_out, bool mg, size_t smem, int ctas_per_sm,
+                      cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    void (*k)(const DetectArgs, const Program);
+    void (*k)(const Launch);
     if (plane_out)
         k = mg ? detect_kernel<DT, G, true, true> : detect_kernel<DT, G, true, false>;
     else
@@ -890,21 +904,21 @@ cudaError_t launch_dg(const DetectArgs &a, const Program &prog, bool plane_out, 
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int64_t grid = tiles < (int64_t)sms * per_sm ? tiles : (int64_t)sms * per_sm;
-    k<<<(unsigned)grid, kThreads, smem, s>>>(a, prog);
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    const int64_t grid = L.n_tiles < (int64_t)sms * per_sm ? L.n_tiles : (int64_t)sms * per_sm;
+    k<<<(unsigned)grid, kThreads, smem, s>>>(L);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 template <int DT>
-cudaError_t launch_detect_dt(const DetectArgs &a, const Program &prog, bool plane_out,
-                             size_t smem, cudaStream_t s) {
-    const bool mg = prog.n_eval > 64;
-    switch (prog.G) {
-        case 8: return launch_dg<DT, 8>(a, prog, plane_out, mg, smem, s);
-        case 16: return launch_dg<DT, 16>(a, prog, plane_out, mg, smem, s);
-        default: return launch_dg<DT, 1>(a, prog, plane_out, mg, smem, s);
+cudaError_t launch_detect_dt(const Launch &L, int G, bool plane_out, bool multi_block,
+                             size_t smem, int ctas_per_sm, cudaStream_t s) {
+    switch (G) {
+        case 8: return launch_dg<DT, 8>(L, plane_out, multi_block, smem, ctas_per_sm, s);
+        case 16: return launch_dg<DT, 16>(L, plane_out, multi_block, smem, ctas_per_sm, s);
+        default: return launch_dg<DT, 1>(L, plane_out, multi_block, smem, ctas_per_sm, s);
     }
 }
 

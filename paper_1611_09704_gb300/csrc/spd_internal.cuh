@@ -88,41 +88,56 @@ struct Group {
 };
 constexpr uint16_t kGroupCoarse = 1;
 
-constexpr int kMaxGroups = 512;
 constexpr int kMaxCodeGroups = 64;          // groups a packed max can tell apart
 constexpr int kMaxEval = SPD_MAX_WIDTHS + 1;
+constexpr int kMaxRanges = 8;               // DM ranges searched by one launch
 
-// The whole width program, passed by value as a __grid_constant__ kernel
-// parameter so that launching needs no host-to-device copy of its own.
-struct Program {
+// The width groups of one range.  Member c of group g is the width
+// g.off + (c + 1) * step (step G for coarse groups, else 1) with eval index
+// g.widx0 + c; eval index 0 is width 1.
+struct RangeProg {
     int32_t n_groups;
     int32_t n_eval;     // evaluated widths: width 1 first, then the listed ones
     int32_t wmax;
     int32_t G;          // step of the coarse window sums, 0 if unused
-    Group groups[kMaxGroups];
-    uint16_t eval_w[kMaxEval];
+    Group groups[kMaxCodeGroups];
 };
 
-struct DetectArgs {
+// One DM range (a plane with its own widths, MSD and threshold) of a launch.
+struct RangeDesc {
     const void *data;
     int64_t n_dm, n_samp, stride;
     const float *scale, *offset;
-    int vec_ok;                 // 16-byte aligned rows: bulk (TMA) copies allowed
-    int per_row;                // MSD scope entry = row (else entry 0)
     const float *inv_tab;       // [entries][n_eval]: 1 / sigma_w, FP32
     const float2 *mu_tab;       // [entries]: mean split into hi + lo FP32
     const int32_t *flags;       // [entries]: nonzero = degenerate sigma
-    int R;                      // blocks of 16 positions staged per tile
-    int span;                   // positions of one tile's window (tile + wmax - 1)
-    int raw_bytes;              // bytes of one raw staging buffer (multiple of 16)
+    int64_t tile0;              // first launch-wide tile index of this range
     int64_t tiles_per_row;
+    int32_t vec_ok;             // 16-byte aligned rows: bulk (TMA) copies allowed
+    int32_t per_row;            // MSD scope entry = row (else entry 0)
+    int32_t R;                  // blocks of 16 positions staged per tile
+    int32_t span;               // positions of one tile's window (tile + wmax - 1)
+    int32_t dm_offset;          // added to the row index in candidate records
     float threshold;
+    RangeProg prog;
+};
+
+// Everything one detect launch needs, passed by value as a __grid_constant__
+// kernel parameter (no host-to-device copy of its own, so it can be captured
+// in a CUDA graph).
+struct Launch {
+    int32_t n_ranges;
+    int32_t R;                  // shared arrays sized for the widest range
+    int32_t raw_bytes;          // bytes of one raw staging buffer (multiple of 16)
+    int32_t max_eval;
+    int64_t n_tiles;
     spd_candidate *out;
     int64_t capacity;
     spd_result *result;
-    float *snr_out;
+    float *snr_out;             // plane output (single range) or null
     uint16_t *width_out;
     int64_t out_stride;
+    RangeDesc rng[kMaxRanges];
 };
 
 struct ConstArgs {
@@ -140,13 +155,13 @@ cudaError_t launch_msd_partial(const MsdArgs &a, int dtype, cudaStream_t s);
 cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t units_per_row,
                              int64_t n_samp, int per_row, MsdPart *scratch, int n_scratch,
                              spd_msd_stats *out, cudaStream_t s);
-cudaError_t launch_consts(const ConstArgs &a, const Program &prog, cudaStream_t s);
+cudaError_t launch_consts(const ConstArgs &a, const RangeProg &prog, cudaStream_t s);
 int nmax_blocks(int nmax);
 int64_t nmax_tiles_per_row(int64_t n_samp);
 cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
                         spd_msd_stats *out, cudaStream_t s);
-cudaError_t launch_detect(const DetectArgs &a, const Program &prog, int dtype, bool plane_out,
-                          size_t smem, cudaStream_t s);
+cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
+                          size_t smem, int ctas_per_sm, cudaStream_t s);
 cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,
                              int64_t n_samp, int64_t stride, float thr, spd_candidate *out,
                              int64_t capacity, spd_result *result, cudaStream_t s);

@@ -275,10 +275,22 @@ __global__ void __launch_bounds__(kMsdThreads) msd_merge_rows_kernel(const MsdPa
     write_msd(out + r, acc);
 }
 
+// Width of eval index k: member k - widx0 of the group holding k.
+__device__ __forceinline__ int eval_width(const RangeProg &prog, int k) {
+    for (int gi = 0; gi < prog.n_groups; ++gi) {
+        const Group g = prog.groups[gi];
+        if (k >= g.widx0 && k < g.widx0 + g.count) {
+            const int d = (g.flags & kGroupCoarse) ? prog.G : 1;
+            return g.off + (k - g.widx0 + 1) * d;
+        }
+    }
+    return 0;
+}
+
 // Step (c) constants: per scope entry e and eval index k, 1/sigma_w in FP32
 // (sigma_w in FP64 from Eq. 4 or Eq. 5), and the mean split as hi + lo FP32.
 __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
-                                                     const __grid_constant__ Program prog) {
+                                                     const __grid_constant__ RangeProg prog) {
     const int e = blockIdx.x;
     const spd_msd_stats m = a.msd[e];
     bool deg = m.status != SPD_OK || !(m.sd > 0.0) || !isfinite(m.sd) || !isfinite(m.mean);
@@ -287,7 +299,7 @@ __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
     if (a.sigma_mode != SPD_SIGMA_SQRTN && (m.nmax < 2 || !(m.sd_nmax > 0.0) || !isfinite(m.sd_nmax)))
         deg = true;
     for (int k = threadIdx.x; k < prog.n_eval; k += blockDim.x) {
-        const double w = (double)prog.eval_w[k];
+        const double w = (double)eval_width(prog, k);
         double sw = sqrt(w) * m.sd;
         if (a.sigma_mode == SPD_SIGMA_LINEAR)
             sw += (w - 1.0) * m.sd_nmax / (nm - 1.0);
@@ -483,7 +495,7 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
     return cudaGetLastError();
 }
 
-cudaError_t launch_consts(const ConstArgs &a, const Program &prog, cudaStream_t s) {
+cudaError_t launch_consts(const ConstArgs &a, const RangeProg &prog, cudaStream_t s) {
     consts_kernel<<<a.entries, 256, 0, s>>>(a, prog);
     return cudaGetLastError();
 }

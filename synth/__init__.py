@@ -199,3 +199,24 @@ def to_host_numpy(t: torch.Tensor) -> np.ndarray:
     if t.dtype == torch.float32:
         return t.numpy()
     return t.view(torch.int16).numpy().view(np.uint16)
+
+
+# Decimations and shapes of the batched form: four DM ranges searched at time
+# decimation 1/2/4/8 with widths 1..64 / 1..128 / 1..256 / 1..512 (decimated
+# samples).
+BATCHED_RANGES = [(2048, 524288, 1, 64), (1536, 262144, 2, 128), (1024, 131072, 4, 256),
+                  (512, 65536, 8, 512)]
+
+
+def batched_ranges(scale: float = 1.0, *, device="cpu", seed=1611_4, pulses_per_range=50):
+    """The batched form's ranges as SynthPlanes: N(0, 1) noise with Gaussian
+    pulses as in the SKA-like recipe (no drift); `scale` shrinks the DM count
+    of each range (tests).  Returns [(SynthPlane, decimation, widths)]."""
+    out = []
+    for k, (n_dm, n_samp, dec, wmax) in enumerate(BATCHED_RANGES):
+        nd = max(1, int(round(n_dm * scale)))
+        sp = ska_like(nd, n_samp, n_pulses=max(1, int(pulses_per_range * scale)), mean=0.0,
+                      sd=1.0, drift_amp=0.0, fwhm_range=(1.0, min(200.0, wmax)), device=device,
+                      seed=seed + k)
+        out.append((sp, dec, list(range(1, wmax + 1))))
+    return out

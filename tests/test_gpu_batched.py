@@ -1,0 +1,99 @@
+"""The batched search (several DM ranges in one persistent launch, captured in
+a CUDA graph) against per-range searches, and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def spd():
+    import paper_1611_09704_gb300 as m
+    m.build()
+    m.load()
+    return m
+
+
+def _key(recs):
+    return np.sort(recs, order=["dm", "sample"])
+
+
+def _specs(spd, scale=0.02):
+    specs, off = [], 0
+    for sp, dec, widths in synth.batched_ranges(scale, device=DEV, seed=5):
+        specs.append(spd.RangeSpec(sp.data, widths, 6.0, dm_offset=off, decimation=dec))
+        off += sp.n_dm
+    # a range whose widths step by 8 (its own launch class) and a per-row one
+    sp = synth.ska_like(5, 30000, n_pulses=4, device=DEV, seed=9)
+    specs.append(spd.RangeSpec(sp.data, list(range(1, 17)) + list(range(24, 257, 8)), 7.0,
+                               dm_offset=off))
+    off += 5
+    sp2 = synth.ska_like(3, 20000, n_pulses=2, device=DEV, seed=10)
+    specs.append(spd.RangeSpec(sp2.data, list(range(1, 33)), 6.0, scope=1, dm_offset=off))
+    return specs
+
+
+def _single(spd, specs):
+    recs = []
+    for r in specs:
+        out, res, _ = spd.search(r.x, r.widths, r.threshold, 2_000_000, r.sigma_mode, r.scope,
+                                 r.nmax)
+        c, st = spd.read_result(res)
+        assert st == 0
+        a = spd.candidates_to_numpy(out, c).copy()
+        a["dm"] += r.dm_offset
+        recs.append(a)
+    return _key(np.concatenate(recs))
+
+
+def test_batched_equals_per_range_searches(spd):
+    specs = _specs(spd)
+    want = _single(spd, specs)
+    out, res, msd = spd.search_batched(specs, 2_000_000)
+    c, st = spd.read_result(res)
+    assert st == 0 and c == want.size
+    got = _key(spd.candidates_to_numpy(out, c))
+    assert np.array_equal(got, want)
+    m = spd.msd_to_numpy(msd)
+    assert m.size == sum(1 if r.scope == 0 else r.x.shape[0] for r in specs)
+
+
+@pytest.mark.parametrize("tuning", [{"ctas_per_sm": 1, "group_scale": 2},
+                                    {"ctas_per_sm": 0, "group_scale": 4}])
+def test_batched_graph_replays(spd, tuning):
+    """A captured graph replayed twice gives the per-range results each time
+    (a different group size changes the grouping, not the answers beyond the
+    stated tolerance: compare candidate sets and SNRs)."""
+    specs = _specs(spd)
+    want = _single(spd, specs)
+    bs = spd.BatchedSearch(specs, 2_000_000, tuning=tuning, graph=True)
+    for _ in range(2):
+        out, res = bs.run()
+        torch.cuda.synchronize()
+        c, st = spd.read_result(res)
+        got = _key(spd.candidates_to_numpy(out, c))
+        assert st == 0
+        band = np.abs(want["snr"] - 6.0) < 1e-3
+        gk = set(zip(got["dm"].tolist(), got["sample"].tolist()))
+        wk = set(zip(want["dm"].tolist(), want["sample"].tolist()))
+        sym = gk ^ wk
+        assert len(sym) <= int(band.sum()) + 2
+        common = np.isin(want["dm"] * 10 ** 7 + want["sample"], got["dm"] * 10 ** 7 + got["sample"])
+        w = want[common]
+        g = got[np.isin(got["dm"] * 10 ** 7 + got["sample"], w["dm"] * 10 ** 7 + w["sample"])]
+        assert np.allclose(g["snr"], w["snr"], rtol=1e-4, atol=1e-4)
+
+
+def test_autotune_picks_a_candidate(spd, tmp_path):
+    from paper_1611_09704_gb300 import autotune
+    specs = _specs(spd, scale=0.01)[:2]
+    path = str(tmp_path / "tune.json")
+    r1 = autotune.autotune(specs, 1_000_000, cache_path=path, reps=2)
+    assert r1["tuning"] in autotune.CANDIDATES and not r1["cached"]
+    r2 = autotune.autotune(specs, 1_000_000, cache_path=path, reps=2)
+    assert r2["cached"] and r2["tuning"] == r1["tuning"]
