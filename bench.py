@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -51,6 +52,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
+    ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched"],
+                    default="ska",
+                    help="ska: the SKA-like FP32 chunk (default, the headline); plain: 64 x 65536 "
+                         "FP32 noise + top-hats; precision: the SKA-like chunk stored as FP16 / "
+                         "BF16 with Eq. 5; batched: four decimated DM ranges in one launch")
+    ap.add_argument("--dtype", choices=["f16", "bf16"], default="f16")
+    ap.add_argument("--report-rows", type=int, default=64)
     return ap.parse_args()
 
 
@@ -327,8 +335,172 @@ def e2e(spd, x, out, res, msd, ws, cap, count, steps, n, dev):
             "api": "spd_search (C ABI) with pinned host buffers"}
 
 
+def timed(step, steps, warmup, clocks_dev):
+    """Warm up, then time `steps` calls of step() with CUDA events."""
+    import torch
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk = Clocks(clocks_dev)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, clk.stop()
+
+
+def run_other(a):
+    """The other configurations of the search, one JSON line each."""
+    import torch
+
+    import oracle
+    import paper_1611_09704_gb300 as spd
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    spd.build()
+    spd.load()
+    hbm, peak_kind = peaks()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "workload_kind": a.workload}
+
+    if a.workload == "plain":
+        sp = synth.plain_tophat(64, 65536, device=dev, seed=1611_0)
+        widths, thr = list(range(1, 33)), 6.0
+        n = 64 * 65536
+        out = torch.empty((1 << 20, 4), dtype=torch.int32, device=dev)
+        res = torch.zeros(16, dtype=torch.uint8, device=dev)
+        msd = torch.empty(40, dtype=torch.uint8, device=dev)
+        ws = torch.empty(spd.search_workspace_bytes(sp.data, widths, thr), dtype=torch.uint8,
+                         device=dev)
+        step = lambda: spd.search(sp.data, widths, thr, out.shape[0], out=out, result=res,
+                                  msd_out=msd, workspace=ws)
+        ms, clocks = timed(step, a.steps, a.warmup, 0)
+        count = spd.read_result(res)[0]
+        line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    candidates_per_step=count, gpu_launches=5 * a.steps,
+                    realtime_factor=65536 * SAMPLE_TIME_S / (ms / 1e3),
+                    config={"workload": "plain FP32 64 DM x 65536, N(0,1) + top-hats "
+                                        "{1,3,8,17,30}; widths 1..32; f_T 6; sqrt(N) sigma",
+                            "l2": "L2-resident (16.8 MB): latency-bound, no roofline"})
+        print(json.dumps(line))
+        return 0
+
+    if a.workload == "precision":
+        n_dm, n_samp = a.n_dm, a.n_samp
+        sp = synth.ska_like(n_dm, n_samp, device=dev, seed=1611_2)
+        n_train = max(1, int(round(0.05 * n_dm)))
+        g = torch.Generator().manual_seed(1611_3)
+        rows = torch.randperm(n_dm, generator=g)[:n_train].tolist()
+        for r in rows:   # a 4000-sample pulse train at matched SNR 200 per row
+            synth.inject_pulse_train(sp.data, r, 100000, 125, 8, 32, 200 * 12.0 / math.sqrt(1000),
+                                     n_samp)
+        rr = min(a.report_rows, n_dm)
+        ref_rows = sorted(set(rows[: rr // 4]) | set(range(rr - len(rows[: rr // 4]))))[:rr]
+        ref32 = sp.data[ref_rows].clone()
+        q = synth.quantise_rows(sp, a.dtype)
+        del sp
+        torch.cuda.empty_cache()
+        widths = WIDTHS
+        x, scale = q.data, q.scale
+        n = n_dm * n_samp
+        out = torch.empty((int(n * 0.45) + 1024, 4), dtype=torch.int32, device=dev)
+        res = torch.zeros(16, dtype=torch.uint8, device=dev)
+        msd = torch.empty(40, dtype=torch.uint8, device=dev)
+        modes = {}
+        for mode, name in ((1, "eq5_as_printed"), (2, "eq5_linear_excess")):
+            ws = torch.empty(spd.search_workspace_bytes(x, widths, THRESHOLD, mode, 0, 256,
+                                                        scale=scale), dtype=torch.uint8,
+                             device=dev)
+            step = lambda: spd.search(x, widths, THRESHOLD, out.shape[0], mode, 0, 256,
+                                      out=out, result=res, msd_out=msd, workspace=ws, scale=scale)
+            ms, clocks = timed(step, a.steps, a.warmup, 0)
+            cnt = spd.read_result(res)[0]
+            m = spd.msd_to_numpy(msd)[0]
+            modes[name] = {"value": n / (ms / 1e3), "ms_per_step": ms, "candidates": cnt,
+                           "mean": float(m["mean"]), "sd": float(m["sd"]),
+                           "sd_nmax": float(m["sd_nmax"]), "clocks": clocks}
+        # quantisation error against the FP64 oracle on the unquantised signal
+        qs = synth.quantise_rows(synth.SynthPlane(ref32, n_samp), a.dtype)
+        err = precision_report(spd, oracle, synth, ref32, qs, widths, dev)
+        main_ = modes["eq5_as_printed"]
+        in_bytes = n * x.element_size()
+        line.update(value=main_["value"], ms_per_step=main_["ms_per_step"], dtype=a.dtype,
+                    clocks=main_["clocks"], candidates_per_step=main_["candidates"],
+                    gpu_launches=8 * a.steps, modes=modes, error_vs_fp64_oracle=err,
+                    realtime_factor=n_samp * SAMPLE_TIME_S / (main_["ms_per_step"] / 1e3),
+                    whole_step_hbm_frac=(3 * in_bytes + 16 * main_["candidates"]) /
+                    (main_["ms_per_step"] / 1e3) / 1e9 / hbm,
+                    config={"workload": f"SKA-like chunk {n_dm} x {n_samp} stored as {a.dtype} "
+                                        "with per-row scale; 5% rows with a 4000-sample pulse "
+                                        "train (SNR 200); widths 1..16 + 24..256/8; f_T 7; Eq. 5 "
+                                        "with sigma_Nmax at Nmax = 256",
+                            "l2": "inputs larger than L2"})
+        print(json.dumps(line))
+        return 0
+
+    if a.workload == "batched":
+        from paper_1611_09704_gb300 import autotune
+        specs, off, n, dur = [], 0, 0, 0.0
+        planes = synth.batched_ranges(1.0, device=dev)
+        for sp, dec, widths in planes:
+            specs.append(spd.RangeSpec(sp.data, widths, THRESHOLD, dm_offset=off, decimation=dec))
+            off += sp.n_dm
+            n += sp.n_dm * sp.n_samp
+            dur = sp.n_samp * dec * SAMPLE_TIME_S
+        cap = 1 << 24
+        tune = autotune.autotune(specs, cap, reps=3)
+        bs = spd.BatchedSearch(specs, cap, tuning=tune["tuning"], graph=True)
+        ms, clocks = timed(lambda: bs.run(), a.steps, a.warmup, 0)
+        cnt = spd.read_result(bs.result)[0]
+        in_bytes = n * 4
+        line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    candidates_per_step=cnt, gpu_launches=(5 * len(specs) + 1) * a.steps,
+                    tuning=tune, realtime_factor=dur / (ms / 1e3),
+                    whole_step_hbm_frac=(2 * in_bytes + 16 * cnt) / (ms / 1e3) / 1e9 / hbm,
+                    config={"workload": "4 DM ranges, decimation 1/2/4/8: 2048x524288, "
+                                        "1536x262144, 1024x131072, 512x65536 FP32 N(0,1) + "
+                                        "Gaussian pulses; widths 1..64/128/256/512; f_T 7; "
+                                        "one persistent launch in a CUDA graph",
+                            "samples": n, "l2": "inputs larger than L2 (6.58 GB)"})
+        print(json.dumps(line))
+        return 0
+    raise SystemExit(f"unknown workload {a.workload}")
+
+
+def precision_report(spd, oracle, synth, ref32, qs, widths, dev):
+    """mu, sigma, sigma_Nmax and SNR of the GPU on the quantised rows against
+    the FP64 oracle on the same rows before quantisation."""
+    import numpy as np
+    import torch
+    x64 = oracle.Plane(synth.to_host_numpy(ref32))
+    mean, sd, sdn, tab = oracle.msd_and_sigma(x64, widths, 1, 0, 256)
+    best, win = oracle.boxcar_snr(x64, mean, sd, tab, widths)
+    m = spd.msd(qs.data, 0, 256, scale=qs.scale)
+    snr, w = spd.boxcar_snr(qs.data, m, widths, 1, 0, scale=qs.scale)
+    torch.cuda.synchronize()
+    g = spd.msd_to_numpy(m)[0]
+    s = snr.cpu().numpy().astype(np.float64)
+    cand = best >= THRESHOLD
+    rel = np.abs(s - best) / np.maximum(np.abs(best), 1.0)
+    return {"rows": int(ref32.shape[0]), "mean_abs_err": abs(float(g["mean"]) - float(mean[0])),
+            "sd_rel_err": abs(float(g["sd"]) / float(sd[0]) - 1),
+            "sd_nmax_rel_err": abs(float(g["sd_nmax"]) / float(sdn[0]) - 1),
+            "snr_err_max_all": float(rel.max()), "snr_err_rms_all": float(np.sqrt((rel ** 2).mean())),
+            "snr_err_max_candidates": float(rel[cand].max()) if cand.any() else None,
+            "candidates_fp64": int(cand.sum()),
+            "candidates_quantised": int((s >= THRESHOLD).sum())}
+
+
 def main():
     a = parse()
+    if a.workload != "ska" and a.impl == "spd":
+        return run_other(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
