@@ -288,6 +288,64 @@ spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
                               spd_result *result_dev, spd_msd_stats *msd_out_dev,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------------------------- streaming
+ * A beam delivers its DM x time data in chunks (all chunks of a beam: same
+ * n_dm, storage type and per-row scale/offset).  The caller owns a device
+ * state buffer (spd_stream_state_bytes) and a host spd_stream_info the calls
+ * keep up to date.  The state holds the running MSD of every sample pushed so
+ * far (Eq. 2 adds each chunk to it, so mu and sigma are those of all data seen,
+ * as Sec. 2.1 defines them for the dataset) and the last wmax - 1 samples of
+ * each row (the halo).  A push searches every start whose full window is
+ * available -- the halo's starts first, then the chunk's -- with the MSD
+ * including that chunk, and holds the last wmax - 1 starts back for the next
+ * push; spd_stream_flush searches the held-back starts at the end of the
+ * stream with the row-end truncation of the one-shot calls.  The first push
+ * with data copies the per-row scale / offset into the state (for the flush);
+ * every chunk of the beam must carry the same values.  Candidate
+ * samples count from the first sample of the stream.  sigma modes other than
+ * SQRTN are unsupported in streaming. */
+typedef struct {
+    int64_t n_dm;
+    int32_t dtype;
+    int32_t msd_scope;
+    int64_t seen;       /* samples per row pushed so far */
+    int64_t halo;       /* samples per row held in the state, not yet searched */
+    int64_t chunks;     /* pushes so far */
+    int32_t wmax;
+    int32_t halo_cap;   /* halo capacity per row in the state (>= wmax - 1) */
+    int32_t has_scale;  /* the beam's chunks carry row_scale (set by the first push) */
+    int32_t has_offset; /* ... row_offset */
+} spd_stream_info;
+
+size_t spd_stream_state_bytes(int64_t n_dm, int32_t dtype, const spd_search_params *params);
+size_t spd_stream_workspace_bytes(int64_t n_dm, int64_t max_chunk, int32_t dtype,
+                                  const spd_search_params *params);
+/* Start a stream: zero the running MSD, empty the halo, fill *info. */
+spd_status spd_stream_reset(spd_stream_info *info, void *state_dev, int64_t n_dm, int32_t dtype,
+                            const spd_search_params *params, void *stream);
+/* Search one chunk (n_samp <= the max_chunk the workspace was sized for).
+ * chunk->data may be device memory or page-locked host memory (the chunk is
+ * first copied into the workspace on `stream`; pageable host memory makes
+ * that copy synchronous); row_scale / row_offset are device pointers.  msd_out_dev: optional device spd_msd_stats (1 or n_dm) receiving
+ * the running MSD used.  Result semantics as spd_search. */
+spd_status spd_stream_push(spd_stream_info *info, void *state_dev, const spd_plane *chunk,
+                           const spd_search_params *params, spd_candidate *out,
+                           int64_t capacity, spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                           void *workspace, size_t workspace_bytes, void *stream);
+/* Where in a push workspace the caller may write a chunk of n_samp samples per
+ * row ([n_dm] rows, *row_stride elements apart, 16-byte aligned rows not
+ * guaranteed) so that the next spd_stream_push of this stream, given a plane
+ * with exactly that data pointer and row_stride and the same workspace, reads
+ * it in place instead of copying it.  Valid until that push. */
+spd_status spd_stream_chunk_view(const spd_stream_info *info, const spd_search_params *params,
+                                 int64_t n_samp, void *workspace, size_t workspace_bytes,
+                                 void **data, int64_t *row_stride);
+/* Search the held-back starts (end of stream); the state stays valid. */
+spd_status spd_stream_flush(spd_stream_info *info, void *state_dev,
+                            const spd_search_params *params, spd_candidate *out,
+                            int64_t capacity, spd_result *result_dev, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 /* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
  * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */
 spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out,

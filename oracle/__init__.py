@@ -16,6 +16,8 @@ numpy arrays.  Function by function:
 - :func:`boxcar_sums`, :func:`boxcar_snr` -- Sec. 2.3 and Algorithm 1.
 - :func:`threshold` -- Sec. 2.4.
 - :func:`search` -- the four steps in order.
+- :func:`stream_replay` -- the same search over a stream delivered in chunks
+  (running MSD, held-back starts, end-of-stream flush).
 """
 from __future__ import annotations
 
@@ -303,3 +305,52 @@ def search(plane, widths, thr, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=
     r0 = rows[0] if rows else 0
     cands = threshold(best, win, thr, row0=r0)
     return cands, best, win, (mean, sd, sdn, tab)
+
+
+# ----------------------------------------------------------------- streaming
+
+def stream_replay(chunks, widths, thr, scope=SCOPE_GLOBAL, dtype="f32", scale=None,
+                  offset=None, detail=False):
+    """The search over a stream delivered as `chunks` ([n_dm, L_k] host arrays:
+    float32, or the uint16 bits of FP16 / BF16 with one per-row scale/offset
+    for the whole stream).  The paper defines one MSD for the dataset
+    (Sec. 2.1) and is silent on streams; the reading followed here: a start i
+    is searched by the first push whose data hold its full window
+    (i + wmax <= samples seen), with the MSD of every sample seen up to and
+    including that push (Eq. 4 sigma_w); the starts no push could finish are
+    searched at the end (flush) with the row-end truncation of Algorithm 1
+    over the whole stream.  Returns one candidate array per push and one for
+    the flush, samples counted from the stream's first sample; with detail,
+    one dict per call instead: cands, lo, hi (the starts searched), mean, sd,
+    best / win over starts [lo, hi) and sub (the plane from sample lo on)."""
+    widths = np.asarray(widths, dtype=np.int32)
+    wmax = int(widths[-1])
+    empty = np.empty(0, dtype=[("dm", np.int32), ("sample", np.int32), ("snr", np.float64),
+                                ("width", np.int32)])
+
+    def search_range(full, lo, hi):
+        # starts [lo, hi) of the stream so far, `full` = every sample seen
+        if full is None or hi <= lo:
+            return dict(cands=empty.copy(), lo=lo, hi=lo) if detail else empty.copy()
+        mean, sd = plane_msd(Plane(full, dtype=dtype, scale=scale, offset=offset), scope)
+        tab = np.stack([sigma_table(SIGMA_SQRTN, sd[e], widths) for e in range(sd.size)])
+        sub = Plane(np.ascontiguousarray(full[:, lo:]), dtype=dtype, scale=scale, offset=offset)
+        best, win = boxcar_snr(sub, mean, sd, tab, widths, scope)
+        best, win = best[:, :hi - lo], win[:, :hi - lo]
+        c = threshold(best, win, thr)
+        c["sample"] += lo
+        if detail:
+            return dict(cands=c, lo=lo, hi=hi, mean=mean, sd=sd, best=best, win=win, sub=sub)
+        return c
+
+    parts, out = [], []
+    emitted = n = 0
+    for ch in chunks:
+        parts.append(np.asarray(ch))
+        n += parts[-1].shape[1]
+        full = np.concatenate(parts, axis=1)
+        hi = max(emitted, n - (wmax - 1))
+        out.append(search_range(full, emitted, hi))
+        emitted = hi
+    out.append(search_range(np.concatenate(parts, axis=1) if parts else None, emitted, n))
+    return out

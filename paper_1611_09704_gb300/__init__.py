@@ -11,4 +11,4 @@ from .binding import (  # noqa: F401
     CAND_DTYPE, MSD_DTYPE, Plane, SpdError, boxcar_snr, boxcar_sums, candidates_to_numpy,
     detect, load, msd, msd_to_numpy, read_result, search, search_workspace_bytes,
     threshold_candidates, widths_to_numpy, RangeSpec, BatchedSearch, search_batched,
-    search_batched_workspace_bytes, SpdTuning)
+    search_batched_workspace_bytes, SpdTuning, BeamStream)

@@ -67,6 +67,14 @@ class SpdTuning(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
+class SpdStreamInfo(ctypes.Structure):
+    _fields_ = [("n_dm", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("msd_scope", ctypes.c_int32), ("seen", ctypes.c_int64),
+                ("halo", ctypes.c_int64), ("chunks", ctypes.c_int64), ("wmax", ctypes.c_int32),
+                ("halo_cap", ctypes.c_int32), ("has_scale", ctypes.c_int32),
+                ("has_offset", ctypes.c_int32)]
+
+
 MSD_BYTES = ctypes.sizeof(SpdMsdStats)      # 40
 CAND_BYTES = ctypes.sizeof(SpdCandidate)    # 16
 RESULT_BYTES = ctypes.sizeof(SpdResult)     # 16
@@ -80,7 +88,9 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_workspace_bytes", "spd_msd", "spd_boxcar_snr_workspace_bytes",
            "spd_boxcar_snr", "spd_threshold_candidates", "spd_detect_workspace_bytes",
            "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums",
-           "spd_msd_noalloc", "spd_search_batched_workspace_bytes", "spd_search_batched"]
+           "spd_msd_noalloc", "spd_search_batched_workspace_bytes", "spd_search_batched",
+           "spd_stream_state_bytes", "spd_stream_workspace_bytes", "spd_stream_reset",
+           "spd_stream_push", "spd_stream_chunk_view", "spd_stream_flush"]
 
 
 class SpdError(RuntimeError):
@@ -145,6 +155,20 @@ def load(path: str | None = None):
     lib.spd_search_batched_workspace_bytes.restype = SZ
     lib.spd_search_batched.argtypes = [pr, I32, pt, P, I64, P, P, P, SZ, P]
     lib.spd_search_batched.restype = I32
+    pi = ctypes.POINTER(SpdStreamInfo)
+    lib.spd_stream_state_bytes.argtypes = [I64, I32, pq]
+    lib.spd_stream_state_bytes.restype = SZ
+    lib.spd_stream_workspace_bytes.argtypes = [I64, I64, I32, pq]
+    lib.spd_stream_workspace_bytes.restype = SZ
+    lib.spd_stream_reset.argtypes = [pi, P, I64, I32, pq, P]
+    lib.spd_stream_reset.restype = I32
+    lib.spd_stream_push.argtypes = [pi, P, pp, pq, P, I64, P, P, P, SZ, P]
+    lib.spd_stream_push.restype = I32
+    lib.spd_stream_chunk_view.argtypes = [pi, pq, I64, P, SZ, ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_int64)]
+    lib.spd_stream_chunk_view.restype = I32
+    lib.spd_stream_flush.argtypes = [pi, P, pq, P, I64, P, P, SZ, P]
+    lib.spd_stream_flush.restype = I32
     _lib = lib
     return lib
 
@@ -455,6 +479,93 @@ class BatchedSearch:
         else:
             self._call(None)
         return self.out, self.result
+
+
+# ---------------------------------------------------------------- streaming
+
+_TD = {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16}
+
+
+class BeamStream:
+    """One beam's stream state (spd_stream_* in include/spd.h): a device state
+    buffer holding the running MSD and the halo, and the host spd_stream_info.
+
+    ``state`` may be a caller-provided uint8 device tensor of at least
+    :meth:`state_bytes` bytes (256-byte aligned).  Every push / flush runs on
+    the given CUDA stream; pushes of one beam must be ordered on the device
+    (same stream, or an event wait) because they share the state."""
+
+    def __init__(self, n_dm, dtype, widths, threshold, scope=MSD_GLOBAL, *, device="cuda",
+                 state=None, stream=None):
+        self.lib = load()
+        self.n_dm = int(n_dm)
+        self.dtype = dtype if isinstance(dtype, int) else _DT[dtype]
+        self.widths = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        self.threshold = float(threshold)
+        self.scope = int(scope)
+        self.params = SpdSearchParams(self.widths.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      self.widths.size, self.threshold, SIGMA_SQRTN,
+                                      self.scope, 0, 0)
+        nb = self.state_bytes()
+        if nb == 0:
+            raise SpdError(SPD_ERR_INVALID_ARG, "spd_stream_state_bytes")
+        self.state = state if state is not None else _workspace(nb, device)
+        self.info = SpdStreamInfo()
+        self.reset(stream)
+
+    def state_bytes(self) -> int:
+        return int(self.lib.spd_stream_state_bytes(self.n_dm, self.dtype,
+                                                   ctypes.byref(self.params)))
+
+    def workspace_bytes(self, max_chunk: int) -> int:
+        return int(self.lib.spd_stream_workspace_bytes(self.n_dm, int(max_chunk), self.dtype,
+                                                       ctypes.byref(self.params)))
+
+    def reset(self, stream=None):
+        _check(self.lib.spd_stream_reset(ctypes.byref(self.info), _ptr(self.state), self.n_dm,
+                                         self.dtype, ctypes.byref(self.params), _stream(stream)),
+               "spd_stream_reset")
+
+    @property
+    def seen(self) -> int:
+        return int(self.info.seen)
+
+    @property
+    def halo(self) -> int:
+        return int(self.info.halo)
+
+    def chunk_view(self, n_samp: int, workspace: torch.Tensor) -> torch.Tensor:
+        """A [n_dm, n_samp] view into ``workspace`` where the next push of this
+        beam reads a chunk in place (the caller fills it, then pushes it)."""
+        ptr, stride = ctypes.c_void_p(), ctypes.c_int64()
+        _check(self.lib.spd_stream_chunk_view(ctypes.byref(self.info), ctypes.byref(self.params),
+                                              int(n_samp), _ptr(workspace), workspace.numel(),
+                                              ctypes.byref(ptr), ctypes.byref(stride)),
+               "spd_stream_chunk_view")
+        td = _TD[self.dtype]
+        eb = torch.empty((), dtype=td).element_size()
+        off = ptr.value - workspace.data_ptr()
+        n = ((self.n_dm - 1) * stride.value + int(n_samp)) * eb
+        flat = workspace[off:off + n].view(td)
+        return flat.as_strided((self.n_dm, int(n_samp)), (stride.value, 1))
+
+    def push(self, chunk, out, capacity, result, workspace, *, msd_out=None, stream=None,
+             **kw):
+        """spd_stream_push of one chunk (a device Plane or tensor)."""
+        pl = as_plane(chunk, **kw)
+        cp = pl.c()
+        _check(self.lib.spd_stream_push(ctypes.byref(self.info), _ptr(self.state),
+                                        ctypes.byref(cp), ctypes.byref(self.params), _ptr(out),
+                                        int(capacity), _ptr(result), _ptr(msd_out),
+                                        _ptr(workspace), workspace.numel(), _stream(stream)),
+               "spd_stream_push")
+
+    def flush(self, out, capacity, result, workspace, *, stream=None):
+        """spd_stream_flush: search the held-back starts at the end of the stream."""
+        _check(self.lib.spd_stream_flush(ctypes.byref(self.info), _ptr(self.state),
+                                         ctypes.byref(self.params), _ptr(out), int(capacity),
+                                         _ptr(result), _ptr(workspace), workspace.numel(),
+                                         _stream(stream)), "spd_stream_flush")
 
 
 # ------------------------------------------------------------------ decoding

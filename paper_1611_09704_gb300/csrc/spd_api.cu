@@ -236,6 +236,8 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
     rd.per_row = scope == SPD_MSD_PER_ROW;
     rd.R = prog_R(prog);
     rd.span = prog_span(prog);
+    rd.n_emit = p->n_samp;
+    rd.sample_base = 0;
     rd.prog = prog;
     return SPD_OK;
 }
@@ -357,6 +359,7 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
         n.offset = plane->row_offset;
         n.msd = out_dev;
         n.per_row = scope == SPD_MSD_PER_ROW;
+        n.vec_ok = plane_vec_ok(plane);
         n.nmax = nmax_sigma;
         n.nb = nmax_blocks(nmax_sigma);
         n.tiles_per_row = L.ntpr;
@@ -580,6 +583,278 @@ spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
         SPD_TRY(run_launch(grp, m, ranges[0].plane.dtype, out, capacity, result_dev, nullptr,
                            nullptr, 0, tuning ? tuning->ctas_per_sm : 0, st));
     }
+    return SPD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Stream state: [entries] MsdPart running MSD, the halo [n_dm][halo_cap], and
+// the beam's per-row scale and offset (copied from its first push).
+struct StreamLayout {
+    int64_t entries;
+    int halo_cap;
+    size_t msd_off, halo_off, scale_off, offset_off, total;
+};
+
+spd_status stream_layout(int64_t n_dm, int32_t dtype, const spd_search_params *params,
+                         RangeProg &prog, StreamLayout &L) {
+    if (n_dm < 1 || n_dm > INT32_MAX || dtype < SPD_F32 || dtype > SPD_BF16)
+        return SPD_ERR_INVALID_ARG;
+    SPD_TRY(check_params(params));
+    if (params->sigma_mode != SPD_SIGMA_SQRTN) return SPD_ERR_UNSUPPORTED;
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    L.entries = params->msd_scope == SPD_MSD_PER_ROW ? n_dm : 1;
+    L.halo_cap = ((prog.wmax - 1) + 7) / 8 * 8;
+    L.msd_off = 0;
+    L.halo_off = align_up((size_t)L.entries * sizeof(MsdPart));
+    L.scale_off = L.halo_off + align_up((size_t)n_dm * L.halo_cap * elem_bytes(dtype));
+    L.offset_off = L.scale_off + align_up((size_t)n_dm * sizeof(float));
+    L.total = L.offset_off + align_up((size_t)n_dm * sizeof(float));
+    return SPD_OK;
+}
+
+// Push workspace: combined [n_dm][cstride] buffer, chunk MSD workspace,
+// msd stats, detect constants.
+struct PushLayout {
+    int64_t cstride;
+    size_t comb_off, msd_off, msd_bytes, stats_off, det_off, total;
+};
+
+PushLayout push_layout(int64_t n_dm, int64_t max_chunk, int32_t dtype, const StreamLayout &S,
+                       const RangeProg &prog) {
+    PushLayout L;
+    const size_t eb = elem_bytes(dtype);
+    L.cstride = (S.halo_cap + max_chunk + 7) / 8 * 8;
+    L.comb_off = 0;
+    L.msd_off = align_up((size_t)n_dm * L.cstride * eb);
+    spd_plane probe;
+    memset(&probe, 0, sizeof(probe));
+    probe.n_dm = n_dm;
+    probe.n_samp = max_chunk > 0 ? max_chunk : 1;
+    L.msd_bytes = msd_layout(&probe).total;
+    L.stats_off = L.msd_off + align_up(L.msd_bytes);
+    L.det_off = L.stats_off + align_up((size_t)S.entries * sizeof(spd_msd_stats));
+    L.total = L.det_off + align_up(det_layout(S.entries, prog.n_eval).total);
+    return L;
+}
+
+spd_status check_info(const spd_stream_info *info, const StreamLayout &S, int32_t dtype,
+                      const spd_search_params *params) {
+    if (!info || info->dtype != dtype || info->msd_scope != params->msd_scope) return SPD_ERR_INVALID_ARG;
+    if (info->halo_cap != S.halo_cap || info->halo < 0 || info->halo > S.halo_cap)
+        return SPD_ERR_INVALID_ARG;
+    return SPD_OK;
+}
+
+// Search the combined buffer [halo | chunk] (n = halo + chunk samples per row)
+// with the running MSD in `stats`; emit starts below n_emit.
+spd_status stream_search(const spd_stream_info *info, const RangeProg &prog,
+                         const spd_search_params *params, const void *comb, int64_t cstride,
+                         int64_t n, int64_t n_emit, const float *scale, const float *offset,
+                         const spd_msd_stats *stats, spd_candidate *out, int64_t cap,
+                         spd_result *result, void *det_ws, cudaStream_t st) {
+    spd_plane cp;
+    memset(&cp, 0, sizeof(cp));
+    cp.data = comb;
+    cp.dtype = info->dtype;
+    cp.n_dm = info->n_dm;
+    cp.n_samp = n;
+    cp.row_stride = cstride;
+    cp.row_scale = scale;
+    cp.row_offset = offset;
+    RangeDesc rd;
+    SPD_TRY(range_consts(&cp, prog, stats, params->msd_scope, params->sigma_mode, result, det_ws,
+                         st, rd));
+    rd.threshold = params->threshold;
+    rd.n_emit = n_emit;
+    rd.sample_base = info->seen - info->halo;
+    return run_launch(&rd, 1, info->dtype, out, cap, result, nullptr, nullptr, 0, 0, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t spd_stream_state_bytes(int64_t n_dm, int32_t dtype, const spd_search_params *params) {
+    RangeProg prog;
+    StreamLayout S;
+    if (stream_layout(n_dm, dtype, params, prog, S) != SPD_OK) return 0;
+    return S.total;
+}
+
+size_t spd_stream_workspace_bytes(int64_t n_dm, int64_t max_chunk, int32_t dtype,
+                                  const spd_search_params *params) {
+    RangeProg prog;
+    StreamLayout S;
+    if (max_chunk < 0 || max_chunk > INT32_MAX) return 0;
+    if (stream_layout(n_dm, dtype, params, prog, S) != SPD_OK) return 0;
+    return push_layout(n_dm, max_chunk, dtype, S, prog).total;
+}
+
+spd_status spd_stream_reset(spd_stream_info *info, void *state_dev, int64_t n_dm, int32_t dtype,
+                            const spd_search_params *params, void *stream) {
+    RangeProg prog;
+    StreamLayout S;
+    SPD_TRY(stream_layout(n_dm, dtype, params, prog, S));
+    if (!info || !state_dev || reinterpret_cast<uintptr_t>(state_dev) % kAlign)
+        return SPD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SPD_CK(launch_zero_parts(reinterpret_cast<MsdPart *>(static_cast<char *>(state_dev) + S.msd_off),
+                             S.entries, st));
+    memset(info, 0, sizeof(*info));
+    info->n_dm = n_dm;
+    info->dtype = dtype;
+    info->msd_scope = params->msd_scope;
+    info->wmax = prog.wmax;
+    info->halo_cap = S.halo_cap;
+    return SPD_OK;
+}
+
+spd_status spd_stream_push(spd_stream_info *info, void *state_dev, const spd_plane *chunk,
+                           const spd_search_params *params, spd_candidate *out,
+                           int64_t capacity, spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+    RangeProg prog;
+    StreamLayout S;
+    if (!info || !chunk) return SPD_ERR_INVALID_ARG;
+    SPD_TRY(stream_layout(info->n_dm, info->dtype, params, prog, S));
+    SPD_TRY(check_info(info, S, chunk->dtype, params));
+    SPD_TRY(check_plane(chunk));
+    if (chunk->n_dm != info->n_dm || !state_dev) return SPD_ERR_INVALID_ARG;
+    // every chunk of a beam carries a per-row scale / offset, or none does
+    if (info->seen > 0 && ((chunk->row_scale != nullptr) != (info->has_scale != 0) ||
+                           (chunk->row_offset != nullptr) != (info->has_offset != 0)))
+        return SPD_ERR_INVALID_ARG;
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    const int64_t L = chunk->n_samp;
+    const size_t eb = elem_bytes(info->dtype);
+    const PushLayout P = push_layout(info->n_dm, L, info->dtype, S, prog);
+    SPD_TRY(check_ws(workspace, workspace_bytes, P.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    char *state = static_cast<char *>(state_dev);
+    MsdPart *run = reinterpret_cast<MsdPart *>(state + S.msd_off);
+    char *halo = state + S.halo_off;
+    char *comb = ws + P.comb_off;
+    const int64_t H = info->halo;
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    if (L == 0) return SPD_OK;
+    if (info->seen == 0) {
+        // the flush has no chunk: keep the beam's scale / offset in the state
+        const size_t rb = (size_t)info->n_dm * sizeof(float);
+        if (chunk->row_scale)
+            SPD_CK(cudaMemcpyAsync(state + S.scale_off, chunk->row_scale, rb,
+                                   cudaMemcpyDeviceToDevice, st));
+        if (chunk->row_offset)
+            SPD_CK(cudaMemcpyAsync(state + S.offset_off, chunk->row_offset, rb,
+                                   cudaMemcpyDeviceToDevice, st));
+        info->has_scale = chunk->row_scale != nullptr;
+        info->has_offset = chunk->row_offset != nullptr;
+    }
+    // [halo | chunk] into the combined buffer
+    if (H > 0)
+        SPD_CK(cudaMemcpy2DAsync(comb, P.cstride * eb, halo, S.halo_cap * eb, H * eb, info->n_dm,
+                                 cudaMemcpyDeviceToDevice, st));
+    const char *src = static_cast<const char *>(chunk->data);
+    if (src == comb + H * eb && chunk->row_stride == P.cstride) {
+        // written in place through spd_stream_chunk_view
+    } else if (src < ws + workspace_bytes && src + (size_t)chunk->n_dm * chunk->row_stride * eb > ws) {
+        return SPD_ERR_INVALID_ARG;  // inside the workspace but not at the view
+    } else {
+        // device or page-locked host memory (unified addressing decides)
+        SPD_CK(cudaMemcpy2DAsync(comb + H * eb, P.cstride * eb, src, chunk->row_stride * eb,
+                                 L * eb, info->n_dm, cudaMemcpyDefault, st));
+    }
+    // running MSD: the chunk's unit partials (read from its place in the
+    // combined buffer) added to the state
+    spd_plane in_place = *chunk;
+    in_place.data = comb + H * eb;
+    in_place.row_stride = P.cstride;
+    const MsdLayout ML = msd_layout(&in_place);
+    MsdArgs ma;
+    ma.data = in_place.data;
+    ma.n_dm = chunk->n_dm;
+    ma.n_samp = L;
+    ma.stride = P.cstride;
+    ma.scale = chunk->row_scale;
+    ma.offset = chunk->row_offset;
+    ma.units_per_row = ML.upr;
+    ma.vec_ok = plane_vec_ok(&in_place);
+    MsdPart *parts = reinterpret_cast<MsdPart *>(ws + P.msd_off);
+    ma.parts = parts;
+    SPD_CK(launch_msd_partial(ma, chunk->dtype, st));
+    spd_msd_stats *stats =
+        msd_out_dev ? msd_out_dev : reinterpret_cast<spd_msd_stats *>(ws + P.stats_off);
+    SPD_CK(launch_stream_msd(parts, info->n_dm, ML.upr, params->msd_scope == SPD_MSD_PER_ROW,
+                             run, stats, st));
+    // search every start with a full window; hold the last wmax - 1 back
+    const int64_t n = H + L;
+    const int64_t hold = n < (int64_t)(prog.wmax - 1) ? n : (int64_t)(prog.wmax - 1);
+    const int64_t n_emit = n - hold;
+    SPD_TRY(stream_search(info, prog, params, comb, P.cstride, n, n_emit, chunk->row_scale,
+                          chunk->row_offset, stats, out, capacity, result_dev, ws + P.det_off, st));
+    if (hold > 0)
+        SPD_CK(cudaMemcpy2DAsync(halo, S.halo_cap * eb, comb + n_emit * eb, P.cstride * eb,
+                                 hold * eb, info->n_dm, cudaMemcpyDeviceToDevice, st));
+    info->seen += L;
+    info->halo = hold;
+    info->chunks += 1;
+    return SPD_OK;
+}
+
+spd_status spd_stream_chunk_view(const spd_stream_info *info, const spd_search_params *params,
+                                 int64_t n_samp, void *workspace, size_t workspace_bytes,
+                                 void **data, int64_t *row_stride) {
+    RangeProg prog;
+    StreamLayout S;
+    if (!info || !data || !row_stride || n_samp < 0 || n_samp > INT32_MAX)
+        return SPD_ERR_INVALID_ARG;
+    SPD_TRY(stream_layout(info->n_dm, info->dtype, params, prog, S));
+    SPD_TRY(check_info(info, S, info->dtype, params));
+    const PushLayout P = push_layout(info->n_dm, n_samp, info->dtype, S, prog);
+    SPD_TRY(check_ws(workspace, workspace_bytes, P.total));
+    *data = static_cast<char *>(workspace) + P.comb_off + info->halo * elem_bytes(info->dtype);
+    *row_stride = P.cstride;
+    return SPD_OK;
+}
+
+spd_status spd_stream_flush(spd_stream_info *info, void *state_dev,
+                            const spd_search_params *params, spd_candidate *out,
+                            int64_t capacity, spd_result *result_dev, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+    RangeProg prog;
+    StreamLayout S;
+    if (!info) return SPD_ERR_INVALID_ARG;
+    SPD_TRY(stream_layout(info->n_dm, info->dtype, params, prog, S));
+    SPD_TRY(check_info(info, S, info->dtype, params));
+    if (!state_dev || !result_dev || capacity < 0 || (capacity > 0 && !out))
+        return SPD_ERR_INVALID_ARG;
+    const PushLayout P = push_layout(info->n_dm, 0, info->dtype, S, prog);
+    SPD_TRY(check_ws(workspace, workspace_bytes, P.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    const int64_t H = info->halo;
+    if (H == 0) return SPD_OK;
+    const size_t eb = elem_bytes(info->dtype);
+    char *ws = static_cast<char *>(workspace);
+    char *state = static_cast<char *>(state_dev);
+    SPD_CK(cudaMemcpy2DAsync(ws + P.comb_off, P.cstride * eb, state + S.halo_off,
+                             S.halo_cap * eb, H * eb, info->n_dm, cudaMemcpyDeviceToDevice, st));
+    spd_msd_stats *stats = reinterpret_cast<spd_msd_stats *>(ws + P.stats_off);
+    SPD_CK(launch_stream_msd(reinterpret_cast<MsdPart *>(ws + P.msd_off), info->n_dm, 0,
+                             info->msd_scope == SPD_MSD_PER_ROW,
+                             reinterpret_cast<MsdPart *>(state + S.msd_off), stats, st));
+    const float *scale = info->has_scale ? reinterpret_cast<const float *>(state + S.scale_off)
+                                         : nullptr;
+    const float *offset = info->has_offset
+                              ? reinterpret_cast<const float *>(state + S.offset_off)
+                              : nullptr;
+    SPD_TRY(stream_search(info, prog, params, ws + P.comb_off, P.cstride, H, H, scale, offset,
+                          stats, out, capacity, result_dev, ws + P.det_off, st));
+    info->halo = 0;
     return SPD_OK;
 }
 

@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
 #pragma unroll
         for (int q = 0; q < kX; ++q) {
             fk.found[q] = -1;
-            if (i0 + q < rd.n_samp && trunc17(best[q]) >= thr) {
+            if (i0 + q < rd.n_emit && trunc17(best[q]) >= thr) {
                 mask |= 1u << q;
                 need |= 1ull << (63u - (__float_as_uint(best[q]) & 63u));
             }
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
                     if (idx < (unsigned long long)L.capacity) {
                         int4 rec;
                         rec.x = rd.dm_offset + (int)row;
-                        rec.y = (int)(i0 + q);
+                        rec.y = (int)(rd.sample_base + i0 + q);
                         rec.z = __float_as_int(snr[q]);
                         rec.w = wdt[q];
                         reinterpret_cast<int4 *>(L.out)[idx] = rec;

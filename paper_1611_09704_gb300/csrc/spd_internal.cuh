@@ -59,6 +59,7 @@ struct NmaxArgs {
     const float *scale, *offset;
     const spd_msd_stats *msd;   // mean used for centring, per scope entry
     int per_row;
+    int vec_ok;                 // rows aligned for 4-element vector loads
     int nmax;
     int nb;                     // staged blocks of 16 samples per tile
     int64_t tiles_per_row;
@@ -119,6 +120,8 @@ struct RangeDesc {
     int32_t span;               // positions of one tile's window (tile + wmax - 1)
     int32_t dm_offset;          // added to the row index in candidate records
     float threshold;
+    int64_t n_emit;             // only starts < n_emit become candidates (n_samp normally)
+    int64_t sample_base;        // added to the start sample in candidate records
     RangeProg prog;
 };
 
@@ -156,6 +159,9 @@ cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t units_p
                              int64_t n_samp, int per_row, MsdPart *scratch, int n_scratch,
                              spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_consts(const ConstArgs &a, const RangeProg &prog, cudaStream_t s);
+cudaError_t launch_stream_msd(const MsdPart *parts, int64_t n_dm, int64_t upr, int per_row,
+                              MsdPart *state, spd_msd_stats *out, cudaStream_t s);
+cudaError_t launch_zero_parts(MsdPart *p, int64_t n, cudaStream_t s);
 int nmax_blocks(int nmax);
 int64_t nmax_tiles_per_row(int64_t n_samp);
 cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,

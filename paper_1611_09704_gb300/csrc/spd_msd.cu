@@ -334,8 +334,10 @@ constexpr int kNmaxPer = kNmaxTile / kMsdThreads;   // 16 consecutive starts per
 template <int DT>
 __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArgs a) {
     using T = typename Elem<DT>::T;
-    extern __shared__ float s_y[];                 // [nb * 16] centred samples
-    float *s_bs = s_y + 16 * a.nb;                 // [nb] block sums
+    // centred samples, 16 positions in 20 words (lane t reading 16t + k with
+    // 128-bit loads hits distinct banks within each quarter warp)
+    extern __shared__ __align__(16) float s_y[];   // [nb * 20]
+    float *s_bs = s_y + 20 * a.nb;                 // [nb] block sums
     const int tid = threadIdx.x;
     const int64_t row = blockIdx.x / a.tiles_per_row;
     const int64_t t0 = (blockIdx.x - row * a.tiles_per_row) * (int64_t)kNmaxTile;
@@ -346,44 +348,88 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArg
     const bool has_sc = a.scale != nullptr;
     const float sc = has_sc ? a.scale[row] : 1.f;
     const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
-    const int npos = 16 * a.nb;
-    for (int p = tid; p < npos; p += kMsdThreads) {
-        float v = 0.f;
-        if (t0 + p < a.n_samp) {
-            v = Elem<DT>::cvt(rp[t0 + p]);
-            if (has_sc) v = fmaf(sc, v, of);
-            v = (v - mh) - ml;
+    for (int q4 = tid; q4 < 4 * a.nb; q4 += kMsdThreads) {
+        const int p = 4 * q4;
+        float x[4];
+        if (a.vec_ok && t0 + p + 3 < a.n_samp) {
+            load4<DT>(rp + t0 + p, x[0], x[1], x[2], x[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                x[e] = t0 + p + e < a.n_samp ? Elem<DT>::cvt(rp[t0 + p + e]) : 0.f;
         }
-        s_y[p] = v;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (has_sc) x[e] = fmaf(sc, x[e], of);
+            x[e] = t0 + p + e < a.n_samp ? (x[e] - mh) - ml : 0.f;
+        }
+        *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+            make_float4(x[0], x[1], x[2], x[3]);
     }
     __syncthreads();
     for (int b = tid; b < a.nb; b += kMsdThreads) {
         float sum = 0.f;
-        for (int q = 0; q < 16; ++q) sum += s_y[16 * b + q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * b + 4 * q);
+            sum += (f.x + f.y) + (f.z + f.w);
+        }
         s_bs[b] = sum;
     }
     __syncthreads();
 
-    Acc acc;
     const int nmax = a.nmax;
     const int p0 = tid * kNmaxPer;                 // first start of this thread (tile-local)
-    // B at p0: whole blocks from p0 to p0 + nmax, corrected by the partial sums
-    // inside the two end blocks (p0 is a multiple of 16)
     const int qe = p0 + nmax;
+    // B at p0: whole blocks from p0 to p0 + nmax (Kahan), plus the partial
+    // block at the end (p0 is a multiple of 16)
     float whole = 0.f, comp = 0.f;
-    for (int b = p0 >> 4; b < (qe >> 4); ++b) {   // Kahan over whole blocks
+    for (int b = p0 >> 4; b < (qe >> 4); ++b) {
         const float y = s_bs[b] - comp;
         const float t = whole + y;
         comp = (t - whole) - y;
         whole = t;
     }
     float tail = 0.f;
-    for (int q = (qe & ~15); q < qe; ++q) tail += s_y[q];
+    for (int q = (qe & ~15); q < qe; ++q) tail += s_y[(q & 15) + 20 * (q >> 4)];
     float B = whole + tail;
-    for (int k = 0; k < kNmaxPer; ++k) {
-        const int64_t i = t0 + p0 + k;
-        if (i + nmax <= a.n_samp) acc.add1(B);
-        B = (B - s_y[p0 + k]) + s_y[p0 + k + nmax];
+    // the thread's 16 samples and the 16 that enter the window as it slides
+    float lo[16], hi[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * tid + 4 * q);
+        lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
+    }
+    if ((nmax & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 f =
+                *reinterpret_cast<const float4 *>(s_y + 20 * (tid + (nmax >> 4)) + 4 * q);
+            hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int q = p0 + k + nmax;
+            hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+        }
+    }
+    float bw[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        bw[k] = B;
+        B = (B - lo[k]) + hi[k];
+    }
+    // starts t0 + p0 + k are full windows while t0 + p0 + k + nmax <= n_samp
+    const int64_t nvalid = a.n_samp - nmax - (t0 + p0) + 1;
+    Acc acc;
+    if (nvalid >= 16) {
+#pragma unroll
+        for (int k = 0; k < 16; k += 4) acc.add4(bw[k], bw[k + 1], bw[k + 2], bw[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < nvalid) acc.add1(bw[k]);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc.merge_down(off);
@@ -432,6 +478,43 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_merge_rows_kernel(const MsdP
     write_nmax(out + r, acc, nmax);
 }
 
+// ------------------------------------------------------------ streaming MSD
+
+// Running MSD of a stream: state[e] holds (n, T, S, min, max) of every sample
+// pushed so far for scope entry e.  The new chunk's unit partials are added
+// with Eq. 2 (state first, then the chunk in unit order) and the result is
+// written back and as spd_msd_stats.  Global scope: one CTA; per row: one
+// thread per row.
+__global__ void __launch_bounds__(kMsdThreads) stream_msd_global_kernel(const MsdPart *parts,
+                                                                       int64_t n_parts,
+                                                                       MsdPart *state,
+                                                                       spd_msd_stats *out) {
+    const MsdPart c = block_merge(parts, 0, n_parts);
+    if (threadIdx.x == 0) {
+        MsdPart s = *state;
+        dmerge(s, c);
+        *state = s;
+        write_msd(out, s);
+    }
+}
+
+__global__ void __launch_bounds__(kMsdThreads) stream_msd_rows_kernel(const MsdPart *parts,
+                                                                     int64_t n_dm, int64_t upr,
+                                                                     MsdPart *state,
+                                                                     spd_msd_stats *out) {
+    const int64_t r = blockIdx.x * (int64_t)kMsdThreads + threadIdx.x;
+    if (r >= n_dm) return;
+    MsdPart s = state[r];
+    for (int64_t u = 0; u < upr; ++u) dmerge(s, parts[r * upr + u]);
+    state[r] = s;
+    write_msd(out + r, s);
+}
+
+__global__ void zero_parts_kernel(MsdPart *p, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = MsdPart{0.0, 0.0, 0.0, 0.0, 0.0};
+}
+
 }  // namespace
 
 cudaError_t launch_msd_partial(const MsdArgs &a, int dtype, cudaStream_t s) {
@@ -472,7 +555,7 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
                         spd_msd_stats *out, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
     if (tiles > 0) {
-        const size_t smem = (size_t)a.nb * 17 * sizeof(float);
+        const size_t smem = (size_t)a.nb * 21 * sizeof(float);
         switch (dtype) {
             case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
             case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
@@ -492,6 +575,23 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
     const int64_t per = (tiles + n1 - 1) / n1;
     msd_merge_l1_kernel<<<(unsigned)n1, kMsdThreads, 0, s>>>(a.parts, tiles, per, scratch);
     nmax_merge_final_kernel<<<1, kMsdThreads, 0, s>>>(scratch, (int)n1, a.nmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_msd(const MsdPart *parts, int64_t n_dm, int64_t upr, int per_row,
+                              MsdPart *state, spd_msd_stats *out, cudaStream_t s) {
+    if (per_row) {
+        const unsigned g = (unsigned)((n_dm + kMsdThreads - 1) / kMsdThreads);
+        if (g) stream_msd_rows_kernel<<<g, kMsdThreads, 0, s>>>(parts, n_dm, upr, state, out);
+    } else {
+        stream_msd_global_kernel<<<1, kMsdThreads, 0, s>>>(parts, n_dm * upr, state, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_parts(MsdPart *p, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    zero_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n);
     return cudaGetLastError();
 }
 

@@ -220,3 +220,59 @@ def batched_ranges(scale: float = 1.0, *, device="cpu", seed=1611_4, pulses_per_
                       seed=seed + k)
         out.append((sp, dec, list(range(1, wmax + 1))))
     return out
+
+
+# Serving form: beams of 2048 DM trials delivered in chunks of U{8192..65536}
+# samples, N(0, 1) noise, top-hat pulses arriving as a Poisson process in data
+# time.
+@dataclass
+class ServingBeam:
+    beam: int
+    chunks: list              # torch tensors [n_dm, L_k] (storage dtype)
+    lengths: list
+    pulses: list
+
+
+def serving_beams(n_beams=16, n_dm=2048, chunks_per_beam=4, *, length_range=(8192, 65536),
+                  rate_hz=0.5, snr_range=(6.0, 40.0), width_range=(1, 128), adj_range=(1, 8),
+                  dtype="f16", sample_time=SAMPLE_TIME_S, device="cpu", seed=1611_5,
+                  pin_memory=False) -> list:
+    """Per beam: chunk lengths L ~ U{length_range}; N(0, 1) noise; pulses at
+    Poisson times (rate_hz per second of data at `sample_time` sampling) with
+    SNR ~ U(snr_range), top-hat width W ~ U{width_range}, amplitude SNR / sqrt(W),
+    over n_adj ~ U{adj_range} adjacent DM rows; a pulse may straddle chunks.
+    Chunks are stored as `dtype` ("f16", "bf16" or "f32"), copied to
+    page-locked host memory when pin_memory is set."""
+    td = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[dtype]
+    out = []
+    for b in range(n_beams):
+        g = _gen("cpu", seed * 1000 + b)
+        lengths = [_randint(g, length_range[0], length_range[1], "cpu")
+                   for _ in range(chunks_per_beam)]
+        total = sum(lengths)
+        t_data = total * sample_time
+        n_p = int(torch.poisson(torch.tensor([rate_hz * t_data], dtype=torch.float64),
+                                generator=g).item())
+        pulses = []
+        for _ in range(n_p):
+            t0 = _randint(g, 0, total - 1, "cpu")
+            w = _randint(g, width_range[0], width_range[1], "cpu")
+            snr = _uniform(g, *snr_range, "cpu")
+            n_adj = _randint(g, adj_range[0], adj_range[1], "cpu")
+            dm0 = _randint(g, 0, max(0, n_dm - n_adj), "cpu")
+            pulses.append(Pulse(dm0, t0, w, snr, n_adj))
+        chunks = []
+        a = 0
+        for k, L in enumerate(lengths):
+            x = noise_plane(n_dm, L, device=device, seed=seed * 1000 + b * 64 + k + 1)
+            for p in pulses:
+                lo, hi = max(p.sample, a), min(p.sample + int(p.width), a + L)
+                if lo < hi:
+                    x[p.dm:p.dm + p.n_dm, lo - a:hi - a] += p.snr / math.sqrt(p.width)
+            x = x.to(td)
+            if pin_memory:
+                x = x.cpu().pin_memory()
+            chunks.append(x)
+            a += L
+        out.append(ServingBeam(b, chunks, lengths, pulses))
+    return out

@@ -48,6 +48,57 @@ def test_struct_sizes_match_header():
     assert b.MSD_DTYPE.itemsize == 40 and b.CAND_DTYPE.itemsize == 16
 
 
+def test_ctypes_layouts_match_the_c_compiler(tmp_path):
+    """gcc compiles include/spd.h; every struct's size and field offsets equal
+    the ctypes mirror's."""
+    import subprocess
+    from paper_1611_09704_gb300 import binding as b
+    structs = {"spd_plane": b.SpdPlane, "spd_msd_stats": b.SpdMsdStats,
+               "spd_candidate": b.SpdCandidate, "spd_result": b.SpdResult,
+               "spd_search_params": b.SpdSearchParams, "spd_range": b.SpdRange,
+               "spd_tuning": b.SpdTuning, "spd_stream_info": b.SpdStreamInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spd.h"',
+             "int main(void) {"]
+    for cname, ct in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in ct._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True,
+                             text=True).stdout.splitlines():
+        cname, key, val = ln.split()
+        got[(cname, key)] = int(val)
+    for cname, ct in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(ct), cname
+        for f, _ in ct._fields_:
+            assert got[(cname, f)] == getattr(ct, f).offset, (cname, f)
+
+
+def test_stream_host_validation(lib):
+    from paper_1611_09704_gb300.binding import SPD_ERR_INVALID_ARG, SpdStreamInfo
+    prm, keep = _params(np.arange(1, 129))
+    sb = lib.spd_stream_state_bytes(2048, 1, ctypes.byref(prm))
+    # running MSD + halo of 127 samples (rounded to 128) + scale + offset
+    assert sb >= 2048 * 128 * 2 + 2 * 2048 * 4
+    assert lib.spd_stream_workspace_bytes(2048, 65536, 1, ctypes.byref(prm)) > 2048 * 65536 * 2
+    assert lib.spd_stream_state_bytes(0, 1, ctypes.byref(prm)) == 0
+    assert lib.spd_stream_state_bytes(16, 9, ctypes.byref(prm)) == 0
+    lin, k2 = _params(np.arange(1, 9), mode=1)
+    assert lib.spd_stream_state_bytes(16, 0, ctypes.byref(lin)) == 0
+    info = SpdStreamInfo()
+    # misaligned state / no state: rejected on the host
+    assert lib.spd_stream_reset(ctypes.byref(info), ctypes.c_void_p(4097), 16, 0,
+                                ctypes.byref(prm), None) == SPD_ERR_INVALID_ARG
+    assert lib.spd_stream_reset(ctypes.byref(info), None, 16, 0, ctypes.byref(prm),
+                                None) == SPD_ERR_INVALID_ARG
+
+
 def _plane(n_dm=4, n_samp=100, stride=None, data=4096, dtype=0):
     from paper_1611_09704_gb300.binding import SpdPlane
     return SpdPlane(data, dtype, 0, n_dm, n_samp, stride or n_samp, None, None)

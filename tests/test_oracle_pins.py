@@ -362,3 +362,64 @@ def test_snr_at_matches_closed_form():
     want = (w * a + b * (w * i + w * (w - 1) / 2) - w * mu) / sw
     assert oracle.snr_at(ramp, 0, i, w, mu, sw) == pytest.approx(want, rel=1e-15)
     assert math.isnan(oracle.snr_at(ramp, 0, 45, 9, mu, sw))
+
+
+# ------------------------------------------------------------ streaming reading
+
+def _stream_brute(chunks, widths, thr, per_row):
+    """Independent statement of the streaming reading, by enumeration: every
+    start i is scored by the first push whose data end e_k satisfies
+    i + wmax <= e_k (else at the end, e = n, with the row-end truncation),
+    with the population mean / sd (numpy) of all samples before e."""
+    x = np.concatenate([np.asarray(c, np.float64) for c in chunks], axis=1)
+    n_dm, n = x.shape
+    wmax = max(widths)
+    ends = np.cumsum([c.shape[1] for c in chunks])
+    rows = []
+    for i in range(n):
+        e = next((int(t) for t in ends if i + wmax <= t), n)
+        for d in range(n_dm):
+            seen = x[d, :e] if per_row else x[:, :e]
+            mu, sd = seen.mean(), seen.std()
+            best, win = (x[d, i] - mu) / sd, 1
+            for w in widths:
+                if i + w > e:
+                    break
+                s = (x[d, i:i + w].sum() - w * mu) / (math.sqrt(w) * sd)
+                if s > best:
+                    best, win = s, w
+            if best >= thr:
+                rows.append((d, i, best, win))
+    return sorted(rows)
+
+
+@pytest.mark.parametrize("per_row", [False, True])
+def test_stream_replay_brute_force(per_row):
+    rng = np.random.default_rng(5)
+    x = rng.normal(0.0, 1.0, (3, 90)).astype(np.float32)
+    x[1, 40:46] += 2.5
+    x[2, 86:90] += 3.0                      # pulse in the tail: found by the flush
+    chunks = [x[:, :7], x[:, 7:8], x[:, 8:40], x[:, 40:41], x[:, 41:90]]
+    widths, thr = [1, 2, 3, 5, 8], 2.0
+    got = np.concatenate(oracle.stream_replay(chunks, widths, thr, scope=int(per_row)))
+    got.sort(order=["dm", "sample"])
+    want = _stream_brute(chunks, widths, thr, per_row)
+    assert len(got) == len(want) > 0
+    for g, (d, i, s, w) in zip(got, sorted(want)):
+        assert (g["dm"], g["sample"], g["width"]) == (d, i, w)
+        assert g["snr"] == pytest.approx(s, rel=1e-12, abs=1e-12)
+
+
+def test_stream_replay_single_chunk_is_one_shot():
+    """One chunk then the flush covers every start once with the MSD of the
+    whole plane: the same list as the one-shot search."""
+    import synth
+    sp = synth.plain_tophat(8, 3000, device="cpu", seed=9)
+    x = synth.to_host_numpy(sp.data)
+    w = list(range(1, 33))
+    one, *_ = oracle.search(x, w, 6.0)
+    rep = oracle.stream_replay([x], w, 6.0)
+    assert len(rep) == 2
+    allc = np.concatenate(rep)
+    allc.sort(order=["dm", "sample"])
+    assert np.array_equal(one, allc)
