@@ -34,7 +34,8 @@ UNIT = "DM×time samples/s"
 WIDTHS = list(range(1, 17)) + list(range(24, 257, 8))
 THRESHOLD = 7.0
 SAMPLE_TIME_S = 64e-6
-KERNELS_PER_STEP = 5   # msd_partial, msd_merge_l1, msd_merge_final, consts, detect
+# msd_partial, msd_merge_l1, fold_final, merge_shards, consts, detect
+KERNELS_PER_STEP = 6
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "detect_traffic.txt")
 DETECT_SRC = os.path.join(ROOT, "paper_1611_09704_gb300", "csrc", "spd_detect_kernel.cuh")
 
@@ -157,7 +158,9 @@ def workload_config(n_dm, n_samp, world):
                          "24..256/8 (46); f_T 7; sqrt(N) sigma; global MSD"),
             "n_dm": n_dm, "n_samp": n_samp, "n_widths": len(WIDTHS), "threshold": THRESHOLD,
             "dtype_in": "f32", "l2": "inputs larger than L2 (plane %.2f GB)" % (n_dm * n_samp * 4 / 1e9),
-            "parallelism": f"independent chunk per GPU x{world}"}
+            "parallelism": (f"DM-row shards x{world}: {n_dm} rows per GPU, one MSD over all "
+                            f"{n_dm * world} rows (all-gather of 40-byte Chan partials)"
+                            if world > 1 else "one GPU")}
 
 
 # ------------------------------------------------------------------ CPU side
@@ -214,6 +217,7 @@ def run_spd(a, rank, world, local):
 
     import paper_1611_09704_gb300 as spd
     import synth
+    from paper_1611_09704_gb300.sharding import ShardedSearch
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -224,21 +228,19 @@ def run_spd(a, rank, world, local):
     sp = synth.ska_like(n_dm, n_samp, device=dev, seed=1611_1 + rank)
     x = sp.data
     cap = int(n * 0.45) + 1024
-    out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
-    res = torch.zeros(16, dtype=torch.uint8, device=dev)
-    msd = torch.empty(40, dtype=torch.uint8, device=dev)
-    wsb = spd.search_workspace_bytes(x, WIDTHS, THRESHOLD)
-    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    # this rank's DM rows [rank * n_dm, (rank + 1) * n_dm) of the whole plane
+    ss = ShardedSearch(x, WIDTHS, THRESHOLD, cap, dm_offset=rank * n_dm)
+    res = ss.result
     res_host = torch.empty(16, dtype=torch.uint8, pin_memory=True)
     stream = torch.cuda.current_stream()
 
     def step(e0=None, e1=None, e2=None):
         if e0 is not None:
             e0.record(stream)
-        spd.msd(x, out=msd, workspace=ws)
+        ss.msd_step()          # shard partial, all-gather (N > 1), Eq. 2 merge
         if e1 is not None:
             e1.record(stream)
-        spd.detect(x, msd, WIDTHS, THRESHOLD, cap, out=out, result=res, workspace=ws)
+        ss.detect_step()       # fused boxcar + SNR + max + threshold
         if e2 is not None:
             e2.record(stream)
         res_host.copy_(res, non_blocking=True)
@@ -276,6 +278,7 @@ def run_spd(a, rank, world, local):
         total_ms = float(t.item())
     ms_step = total_ms / a.steps
     value = world * n / (ms_step / 1e3)
+    e2e_line = None if a.no_e2e else e2e(ss, x, count, a.e2e_steps, n, world, dev)
     if rank != 0:
         return 0
 
@@ -300,7 +303,7 @@ def run_spd(a, rank, world, local):
             "clocks": clocks}
 
     if not a.no_e2e:
-        line["e2e"] = e2e(spd, x, out, res, msd, ws, cap, count, a.e2e_steps, n, dev)
+        line["e2e"] = e2e_line
     if not a.no_cpu_baseline:
         rows = min(a.cpu_rows, n_dm)
         dt, _, cores = oracle_sample(rows, n_samp, 7)
@@ -312,34 +315,43 @@ def run_spd(a, rank, world, local):
     return 0
 
 
-def e2e(spd, x, out, res, msd, ws, cap, count, steps, n, dev):
-    """spd_search from pinned host memory: H2D of the plane, the search, D2H of
-    the count and of every candidate record, per step."""
+def e2e(ss, x, count, steps, n, world, dev):
+    """The sharded search from pinned host memory: H2D of the rank's rows, the
+    MSD exchange and the search, D2H of the count and of every candidate
+    record, per step; the slowest rank's time."""
     import torch
+    import torch.distributed as dist
     xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
     xh.copy_(x)
     ch = torch.empty((max(count, 1), 4), dtype=torch.int32, pin_memory=True)
     rh = torch.empty(16, dtype=torch.uint8, pin_memory=True)
     times, d2h = [], []
     for k in range(steps + 1):
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         x.copy_(xh, non_blocking=True)
-        spd.search(x, WIDTHS, THRESHOLD, cap, out=out, result=res, msd_out=msd, workspace=ws)
-        rh.copy_(res, non_blocking=True)
+        ss.run()
+        rh.copy_(ss.result, non_blocking=True)
         torch.cuda.synchronize()
         c = int(rh[:8].numpy().view("<u8")[0])
-        m = min(c, cap, ch.shape[0])
-        ch[:m].copy_(out[:m], non_blocking=True)
+        m = min(c, ss.capacity, ch.shape[0])
+        ch[:m].copy_(ss.out[:m], non_blocking=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if k:
             times.append(dt)
             d2h.append(16 + 16 * m)
     t = sum(times) / len(times)
-    return {"value": n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
+    if world > 1:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return {"value": world * n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
             "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3,
-            "api": "spd_search (C ABI) with pinned host buffers"}
+            "api": "ShardedSearch over the C ABI (shard partial, merge, detect) with pinned "
+                   "host buffers"}
 
 
 def timed(step, steps, warmup, clocks_dev):

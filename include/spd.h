@@ -183,6 +183,43 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
 spd_status spd_msd_noalloc(const spd_plane *plane, int32_t scope, spd_msd_stats *out_dev,
                            void *stream);
 
+/* ------------------------------------------------------ DM-row shards
+ * A plane split by DM rows over several GPUs (one shard per rank) shares one
+ * MSD of the whole plane (Sec. 2.1 defines it for the dataset).  Eq. 2 makes
+ * the merge of partials order-free up to rounding, so each rank reduces its
+ * shard to one partial, the ranks exchange partials (an all-gather of
+ * sizeof(spd_msd_part) bytes per rank; the exchange is the caller's), and
+ * every rank merges the gathered array in shard order, which gives every rank
+ * the same bits.  Global scope only: per-row statistics need no exchange.
+ * With one shard the result equals spd_msd's bit for bit. */
+typedef struct {
+    double n;      /* samples */
+    double T;      /* sum */
+    double S;      /* sum of squared deviations from T / n */
+    double lo, hi; /* min and max value (exact constancy test) */
+} spd_msd_part;
+
+/* The shard's partial of the samples (Eq. 1 per thread, Eq. 2 up to one
+ * record) into *part_dev (device, one record).  Workspace: as
+ * spd_msd_workspace_bytes(plane, SPD_MSD_GLOBAL, 0).  Errors: as spd_msd. */
+spd_status spd_msd_shard_partial(const spd_plane *plane, spd_msd_part *part_dev, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+/* Eq. 2 over parts_dev[0 .. n_shards) in that order -> out_dev (one
+ * spd_msd_stats: mean, sd, n, status as spd_msd; sd_nmax 0). */
+spd_status spd_msd_merge_partials(const spd_msd_part *parts_dev, int32_t n_shards,
+                                  spd_msd_stats *out_dev, void *stream);
+/* Eq. 5's sigma_Nmax needs a second exchange: the partial of the shard's
+ * B_Nmax series (full windows within each row), centred on the merged mean
+ * in msd_dev.  Workspace: as spd_msd_workspace_bytes(plane, SPD_MSD_GLOBAL,
+ * nmax_sigma). */
+spd_status spd_sd_nmax_shard_partial(const spd_plane *plane, int32_t nmax_sigma,
+                                     const spd_msd_stats *msd_dev, spd_msd_part *part_dev,
+                                     void *workspace, size_t workspace_bytes, void *stream);
+/* Eq. 2 over the gathered B_Nmax partials in shard order -> sd_nmax and nmax
+ * of out_dev (its other fields are left as they are). */
+spd_status spd_sd_nmax_merge_partials(const spd_msd_part *parts_dev, int32_t n_shards,
+                                      int32_t nmax_sigma, spd_msd_stats *out_dev, void *stream);
+
 /* Bytes of device workspace spd_boxcar_snr needs. */
 size_t spd_boxcar_snr_workspace_bytes(const spd_plane *plane, int32_t scope,
                                       const int32_t *widths, int32_t n_widths);

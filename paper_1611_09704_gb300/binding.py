@@ -75,7 +75,13 @@ class SpdStreamInfo(ctypes.Structure):
                 ("has_offset", ctypes.c_int32)]
 
 
+class SpdMsdPart(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_double), ("T", ctypes.c_double), ("S", ctypes.c_double),
+                ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
+
+
 MSD_BYTES = ctypes.sizeof(SpdMsdStats)      # 40
+PART_BYTES = ctypes.sizeof(SpdMsdPart)      # 40
 CAND_BYTES = ctypes.sizeof(SpdCandidate)    # 16
 RESULT_BYTES = ctypes.sizeof(SpdResult)     # 16
 
@@ -90,7 +96,9 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_search_workspace_bytes", "spd_detect", "spd_search", "spd_boxcar_sums",
            "spd_msd_noalloc", "spd_search_batched_workspace_bytes", "spd_search_batched",
            "spd_stream_state_bytes", "spd_stream_workspace_bytes", "spd_stream_reset",
-           "spd_stream_push", "spd_stream_chunk_view", "spd_stream_flush"]
+           "spd_stream_push", "spd_stream_chunk_view", "spd_stream_flush",
+           "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
+           "spd_sd_nmax_merge_partials"]
 
 
 class SpdError(RuntimeError):
@@ -155,6 +163,14 @@ def load(path: str | None = None):
     lib.spd_search_batched_workspace_bytes.restype = SZ
     lib.spd_search_batched.argtypes = [pr, I32, pt, P, I64, P, P, P, SZ, P]
     lib.spd_search_batched.restype = I32
+    lib.spd_msd_shard_partial.argtypes = [pp, P, P, SZ, P]
+    lib.spd_msd_shard_partial.restype = I32
+    lib.spd_msd_merge_partials.argtypes = [P, I32, P, P]
+    lib.spd_msd_merge_partials.restype = I32
+    lib.spd_sd_nmax_shard_partial.argtypes = [pp, I32, P, P, P, SZ, P]
+    lib.spd_sd_nmax_shard_partial.restype = I32
+    lib.spd_sd_nmax_merge_partials.argtypes = [P, I32, I32, P, P]
+    lib.spd_sd_nmax_merge_partials.restype = I32
     pi = ctypes.POINTER(SpdStreamInfo)
     lib.spd_stream_state_bytes.argtypes = [I64, I32, pq]
     lib.spd_stream_state_bytes.restype = SZ
@@ -258,6 +274,53 @@ def msd(x, scope=MSD_GLOBAL, nmax_sigma=0, *, stream=None, out=None, workspace=N
     ws = workspace if workspace is not None else _workspace(wsb, pl.data.device)
     _check(lib.spd_msd(ctypes.byref(cp), scope, nmax_sigma, _ptr(out), _ptr(ws), wsb,
                        _stream(stream)), "spd_msd")
+    return out
+
+
+def msd_shard_partial(x, *, stream=None, out=None, workspace=None, **kw) -> torch.Tensor:
+    """spd_msd_shard_partial: the shard's spd_msd_part (uint8 device tensor, 40 B)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    if out is None:
+        out = torch.empty(PART_BYTES, dtype=torch.uint8, device=pl.data.device)
+    wsb = lib.spd_msd_workspace_bytes(ctypes.byref(cp), MSD_GLOBAL, 0)
+    ws = workspace if workspace is not None else _workspace(wsb, pl.data.device)
+    _check(lib.spd_msd_shard_partial(ctypes.byref(cp), _ptr(out), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "spd_msd_shard_partial")
+    return out
+
+
+def msd_merge_partials(parts: torch.Tensor, n_shards: int, *, stream=None, out=None):
+    """spd_msd_merge_partials over n_shards gathered parts (shard order)."""
+    lib = load()
+    if out is None:
+        out = torch.empty(MSD_BYTES, dtype=torch.uint8, device=parts.device)
+    _check(lib.spd_msd_merge_partials(_ptr(parts), int(n_shards), _ptr(out), _stream(stream)),
+           "spd_msd_merge_partials")
+    return out
+
+
+def sd_nmax_shard_partial(x, nmax, msd_dev, *, stream=None, out=None, workspace=None, **kw):
+    """spd_sd_nmax_shard_partial: the shard's B_Nmax-series partial."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    if out is None:
+        out = torch.empty(PART_BYTES, dtype=torch.uint8, device=pl.data.device)
+    wsb = lib.spd_msd_workspace_bytes(ctypes.byref(cp), MSD_GLOBAL, int(nmax))
+    ws = workspace if workspace is not None else _workspace(wsb, pl.data.device)
+    _check(lib.spd_sd_nmax_shard_partial(ctypes.byref(cp), int(nmax), _ptr(msd_dev), _ptr(out),
+                                         _ptr(ws), ws.numel(), _stream(stream)),
+           "spd_sd_nmax_shard_partial")
+    return out
+
+
+def sd_nmax_merge_partials(parts: torch.Tensor, n_shards: int, nmax: int, out: torch.Tensor, *,
+                           stream=None):
+    """spd_sd_nmax_merge_partials: sd_nmax / nmax of `out` from the gathered parts."""
+    _check(load().spd_sd_nmax_merge_partials(_ptr(parts), int(n_shards), int(nmax), _ptr(out),
+                                             _stream(stream)), "spd_sd_nmax_merge_partials")
     return out
 
 

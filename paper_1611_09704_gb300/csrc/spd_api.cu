@@ -11,6 +11,8 @@
 
 using namespace spd;
 
+static_assert(sizeof(spd_msd_part) == sizeof(spd::MsdPart), "spd_msd_part layout");
+
 namespace {
 
 thread_local int g_last_cuda_error = 0;
@@ -366,6 +368,88 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
         n.parts = reinterpret_cast<MsdPart *>(base + L.nmax_off);
         SPD_CK(launch_nmax(n, plane->dtype, scratch, kMergeScratch, out_dev, st));
     }
+    return SPD_OK;
+}
+
+spd_status spd_msd_shard_partial(const spd_plane *plane, spd_msd_part *part_dev, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+    SPD_TRY(check_plane(plane));
+    if (!part_dev) return SPD_ERR_INVALID_ARG;
+    const MsdLayout L = msd_layout(plane, 0);
+    SPD_TRY(check_ws(workspace, workspace_bytes, L.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    MsdPart *parts = reinterpret_cast<MsdPart *>(base + L.parts_off);
+    MsdPart *scratch = reinterpret_cast<MsdPart *>(base + L.scratch_off);
+    MsdPart *out = reinterpret_cast<MsdPart *>(part_dev);
+    if (plane_empty(plane)) {
+        SPD_CK(launch_zero_parts(out, 1, st));
+        return SPD_OK;
+    }
+    MsdArgs a;
+    a.data = plane->data;
+    a.n_dm = plane->n_dm;
+    a.n_samp = plane->n_samp;
+    a.stride = plane->row_stride;
+    a.scale = plane->row_scale;
+    a.offset = plane->row_offset;
+    a.units_per_row = L.upr;
+    a.vec_ok = plane_vec_ok(plane);
+    a.parts = parts;
+    SPD_CK(launch_msd_partial(a, plane->dtype, st));
+    SPD_CK(launch_fold_parts(parts, plane->n_dm * L.upr, scratch, kMergeScratch, out, st));
+    return SPD_OK;
+}
+
+spd_status spd_msd_merge_partials(const spd_msd_part *parts_dev, int32_t n_shards,
+                                  spd_msd_stats *out_dev, void *stream) {
+    if (!parts_dev || !out_dev || n_shards < 1) return SPD_ERR_INVALID_ARG;
+    SPD_CK(launch_merge_shards(reinterpret_cast<const MsdPart *>(parts_dev), n_shards, 0, 0,
+                               out_dev, static_cast<cudaStream_t>(stream)));
+    return SPD_OK;
+}
+
+spd_status spd_sd_nmax_shard_partial(const spd_plane *plane, int32_t nmax_sigma,
+                                     const spd_msd_stats *msd_dev, spd_msd_part *part_dev,
+                                     void *workspace, size_t workspace_bytes, void *stream) {
+    SPD_TRY(check_plane(plane));
+    if (!part_dev || !msd_dev || nmax_sigma < 2 || nmax_sigma > SPD_MAX_WIDTH)
+        return SPD_ERR_INVALID_ARG;
+    const MsdLayout L = msd_layout(plane, nmax_sigma);
+    SPD_TRY(check_ws(workspace, workspace_bytes, L.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    MsdPart *scratch = reinterpret_cast<MsdPart *>(base + L.scratch_off);
+    MsdPart *out = reinterpret_cast<MsdPart *>(part_dev);
+    if (plane_empty(plane)) {
+        SPD_CK(launch_zero_parts(out, 1, st));
+        return SPD_OK;
+    }
+    NmaxArgs n;
+    n.data = plane->data;
+    n.n_dm = plane->n_dm;
+    n.n_samp = plane->n_samp;
+    n.stride = plane->row_stride;
+    n.scale = plane->row_scale;
+    n.offset = plane->row_offset;
+    n.msd = msd_dev;
+    n.per_row = 0;
+    n.vec_ok = plane_vec_ok(plane);
+    n.nmax = nmax_sigma;
+    n.nb = nmax_blocks(nmax_sigma);
+    n.tiles_per_row = L.ntpr;
+    n.parts = reinterpret_cast<MsdPart *>(base + L.nmax_off);
+    SPD_CK(launch_nmax_partial(n, plane->dtype, st));
+    SPD_CK(launch_fold_parts(n.parts, plane->n_dm * L.ntpr, scratch, kMergeScratch, out, st));
+    return SPD_OK;
+}
+
+spd_status spd_sd_nmax_merge_partials(const spd_msd_part *parts_dev, int32_t n_shards,
+                                      int32_t nmax_sigma, spd_msd_stats *out_dev, void *stream) {
+    if (!parts_dev || !out_dev || n_shards < 1 || nmax_sigma < 2 || nmax_sigma > SPD_MAX_WIDTH)
+        return SPD_ERR_INVALID_ARG;
+    SPD_CK(launch_merge_shards(reinterpret_cast<const MsdPart *>(parts_dev), n_shards, 1,
+                               nmax_sigma, out_dev, static_cast<cudaStream_t>(stream)));
     return SPD_OK;
 }
 

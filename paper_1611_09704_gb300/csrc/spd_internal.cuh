@@ -164,6 +164,13 @@ cudaError_t launch_stream_msd(const MsdPart *parts, int64_t n_dm, int64_t upr, i
 cudaError_t launch_zero_parts(MsdPart *p, int64_t n, cudaStream_t s);
 int nmax_blocks(int nmax);
 int64_t nmax_tiles_per_row(int64_t n_samp);
+cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s);
+// Fold n_parts partials into *out (the block tree of the final merge).
+cudaError_t launch_fold_parts(const MsdPart *parts, int64_t n_parts, MsdPart *scratch,
+                              int n_scratch, MsdPart *out, cudaStream_t s);
+// Shard partials in shard order -> mean/sd (what 0) or sd_nmax (what 1).
+cudaError_t launch_merge_shards(const MsdPart *parts, int n, int what, int nmax,
+                                spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
                         spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,

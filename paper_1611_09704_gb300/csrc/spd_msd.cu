@@ -478,6 +478,29 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_merge_rows_kernel(const MsdP
     write_nmax(out + r, acc, nmax);
 }
 
+// ------------------------------------------------------------ shard partials
+
+// One block: fold n parts into one with the block tree (as the final merge).
+__global__ void __launch_bounds__(kMsdThreads) fold_final_kernel(const MsdPart *scratch, int n,
+                                                                 MsdPart *out) {
+    const MsdPart r = block_merge(scratch, 0, n);
+    if (threadIdx.x == 0) *out = r;
+}
+
+// Shard partials merged with Eq. 2 in shard order (one thread: the order, and
+// so every bit of the result, is the same on every rank).  what = 0: mean and
+// sd into out; what = 1: sd_nmax of the B_Nmax series.
+__global__ void merge_shards_kernel(const MsdPart *parts, int n, int what, int nmax,
+                                    spd_msd_stats *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    MsdPart acc{0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) dmerge(acc, parts[k]);
+    if (what == 0)
+        write_msd(out, acc);
+    else
+        write_nmax(out, acc, nmax);
+}
+
 // ------------------------------------------------------------ streaming MSD
 
 // Running MSD of a stream: state[e] holds (n, T, S, min, max) of every sample
@@ -551,17 +574,40 @@ cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t upr, in
 int nmax_blocks(int nmax) { return (kNmaxTile + nmax + 15) / 16 + 1; }
 int64_t nmax_tiles_per_row(int64_t n_samp) { return (n_samp + kNmaxTile - 1) / kNmaxTile; }
 
+cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
+    const int64_t tiles = a.n_dm * a.tiles_per_row;
+    if (tiles <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.nb * 21 * sizeof(float);
+    switch (dtype) {
+        case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+        case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+        default: nmax_partial_kernel<SPD_BF16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold_parts(const MsdPart *parts, int64_t n_parts, MsdPart *scratch,
+                              int n_scratch, MsdPart *out, cudaStream_t s) {
+    int64_t n1 = (n_parts + kMsdThreads - 1) / kMsdThreads;
+    if (n1 > n_scratch) n1 = n_scratch;
+    if (n1 < 1) n1 = 1;
+    const int64_t per = (n_parts + n1 - 1) / n1;
+    msd_merge_l1_kernel<<<(unsigned)n1, kMsdThreads, 0, s>>>(parts, n_parts, per, scratch);
+    fold_final_kernel<<<1, kMsdThreads, 0, s>>>(scratch, (int)n1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_shards(const MsdPart *parts, int n, int what, int nmax,
+                                spd_msd_stats *out, cudaStream_t s) {
+    merge_shards_kernel<<<1, 32, 0, s>>>(parts, n, what, nmax, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
                         spd_msd_stats *out, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
-    if (tiles > 0) {
-        const size_t smem = (size_t)a.nb * 21 * sizeof(float);
-        switch (dtype) {
-            case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
-            case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
-            default: nmax_partial_kernel<SPD_BF16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
-        }
-        cudaError_t e = cudaGetLastError();
+    {
+        cudaError_t e = launch_nmax_partial(a, dtype, s);
         if (e != cudaSuccess) return e;
     }
     if (a.per_row) {
