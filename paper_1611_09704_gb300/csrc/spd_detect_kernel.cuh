@@ -554,7 +554,7 @@ __device__ __forceinline__ void load_range_consts(const RangeDesc &rd, int entry
 }
 
 template <int DT, int G, bool PLANE, bool MG>
-__global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_constant__ Launch L) {
+__global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const __grid_constant__ Launch L) {
     using T = typename Elem<DT>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int RM = L.R;
@@ -625,14 +625,18 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
         const int64_t i0 = t0 + (int64_t)tid * kX;   // first start sample of this thread
         const T *rowp = static_cast<const T *>(rd.data) + row * rd.stride;
 
-        if (tma && !mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1))) {
-            // the copy did not land in time: report it, give the copy one more
-            // bounded wait, and leave this CTA
-            if (tid == 0) {
-                if (L.result) atomicExch(&L.result->status, (int)SPD_ERR_TIMEOUT);
-                mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+        if (tma) {
+            const bool ok = mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+            // the whole CTA takes the same decision: if the copy did not land in
+            // time for any thread, report it, give the copy (the only one in
+            // flight) one more bounded wait, and leave
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    if (L.result) atomicExch(&L.result->status, (int)SPD_ERR_TIMEOUT);
+                    mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+                }
+                return;
             }
-            return;
         }
 
         const bool deg = rd.flags[entry] != 0;
@@ -780,8 +784,7 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
         // ------------------------------------------------ candidate search
         const float thr = rd.threshold;
         const float minC = s_mn[tid];
-        FindSink fk;
-        float *best = fk.best;
+        float best[kX];
 #pragma unroll
         for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
         MaxSink mk;
@@ -811,33 +814,23 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
             for (int q = 1; q < kX; ++q) minbest = fminf(minbest, best[q]);
         }
 
-        // candidates and their winning groups
+        // Threshold (Sec. 2.4, inclusive): the candidates and their winning groups
         uint32_t mask = 0;
         uint64_t need = 0;
+        uint32_t wcode[kX / 4];   // winning group code of sample q: byte q & 3 of wcode[q >> 2]
+#pragma unroll
+        for (int q = 0; q < kX / 4; ++q) wcode[q] = 0;
 #pragma unroll
         for (int q = 0; q < kX; ++q) {
-            fk.found[q] = -1;
+            const uint32_t code = __float_as_uint(best[q]) & 63u;
+            wcode[q >> 2] |= code << (8 * (q & 3));
             if (i0 + q < rd.n_emit && trunc17(best[q]) >= thr) {
                 mask |= 1u << q;
-                need |= 1ull << (63u - (__float_as_uint(best[q]) & 63u));
+                need |= 1ull << (63u - code);
             }
         }
-        // recovery: re-evaluate each winning group with the same arithmetic
-        while (need) {
-            const int gi = __ffsll((long long)need) - 1;
-            need &= need - 1;
-            const Group g = rp.groups[gi];
-            fk.code = 63u - (uint32_t)gi;
-            group_start(B, s_y, s_bs, tid, g.off);
-            run_group_compact<G>(B, fk, sy_t, sg_t, g, s_inv);
-        }
-#pragma unroll
-        for (int q = 0; q < kX; ++q) {
-            snr[q] = trunc17(best[q]);
-            wdt[q] = fk.found[q] >= 0 ? (int)s_ew[fk.found[q]] : 0;
-        }
-
-        // Threshold (Sec. 2.4, inclusive) and block-aggregated compaction.
+        // block-aggregated compaction: one atomic per CTA reserves the tile's
+        // records; thread t's records start at idx0
         const int cnt = __popc(mask);
         const int lane = tid & 31, warp = tid >> 5;
         int incl = cnt;
@@ -847,7 +840,9 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
             if (lane >= o) incl += v;
         }
         if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
+        // the barrier that publishes the warp counts also tells whether the
+        // tile has any candidate; most tiles of noise-like data have none
+        if (!__syncthreads_or(cnt)) continue;   // every thread is done with this tile
         if (tid < 32) {
             const int wv = (lane < kThreads / 32) ? s_wsum[lane] : 0;
             int wsc = wv;
@@ -864,25 +859,46 @@ __global__ void __launch_bounds__(kThreads, 2) detect_kernel(const __grid_consta
                                : 0ull;
         }
         __syncthreads();
-        if (cnt) {
-            unsigned long long idx = s_base + (unsigned long long)(s_wsum[warp] + incl - cnt);
+        const unsigned long long idx0 = s_base + (unsigned long long)(s_wsum[warp] + incl - cnt);
+
+        // Recovery and emission: each winning group is evaluated again through
+        // the same path (so bitwise the same SNRs), now keeping a packed (SNR,
+        // eval index) max per sample; a group never straddles a multiple of 64
+        // in eval index, so the code bits give the index.  Among SNRs equal to
+        // 2^-17 relative the smallest width wins, as in the plane output.  For
+        // the samples this group won, its maximum truncated to 2^-17 is the
+        // sample's best SNR.
+        while (need) {
+            const int gi = __ffsll((long long)need) - 1;
+            need &= need - 1;
+            const Group g = rp.groups[gi];
+            PackSink rk;
+#pragma unroll
+            for (int q = 0; q < kX; ++q) rk.best[q] = -INFINITY;
+            group_start(B, s_y, s_bs, tid, g.off);
+            run_group<G>(B, rk, sy_t, sg_t, g, s_inv);
+            const uint32_t gcode = 63u - (uint32_t)gi;
+            const int base = (g.widx0 & ~63) + 63;
 #pragma unroll
             for (int q = 0; q < kX; ++q) {
-                if (mask & (1u << q)) {
+                if (((mask >> q) & 1u) && ((wcode[q >> 2] >> (8 * (q & 3))) & 63u) == gcode) {
+                    const unsigned long long idx =
+                        idx0 + (unsigned long long)__popc(mask & ((1u << q) - 1u));
                     if (idx < (unsigned long long)L.capacity) {
                         int4 rec;
                         rec.x = rd.dm_offset + (int)row;
                         rec.y = (int)(rd.sample_base + i0 + q);
-                        rec.z = __float_as_int(snr[q]);
-                        rec.w = wdt[q];
+                        rec.z = __float_as_int(trunc17(rk.best[q]));
+                        rec.w = (int)s_ew[base - (int)(__float_as_uint(rk.best[q]) & 63u)];
                         reinterpret_cast<int4 *>(L.out)[idx] = rec;
                     }
-                    ++idx;
                 }
             }
         }
-        // no barrier needed here: every warp has passed the emission barriers,
-        // so all reads of this tile's shared arrays are done
+        // the next tile rewrites the shared arrays that recovery reads: with
+        // bulk copies the barrier after the next copy's wait orders that,
+        // otherwise this one
+        if (!tma) __syncthreads();
     }
 }
 
