@@ -160,8 +160,8 @@ int raw_bytes_of(int span, int dtype) { return (int)((span * elem_bytes(dtype) +
 size_t launch_smem(int R, int raw_bytes, int max_eval, int G) {
     size_t b = 16 + 2 * (size_t)raw_bytes;
     b += (size_t)(G ? 2 : 1) * 20 * R * sizeof(float);
-    b += (size_t)R * 3 * sizeof(float);
-    b += (size_t)max_eval * sizeof(float) + kMaxCodeGroups * sizeof(float);
+    b += (size_t)R * (3 + 5) * sizeof(float);   // block sums, max/min prefix, max table
+    b += (size_t)max_eval * sizeof(float) + 16 + kMaxCodeGroups * 16;
     b += (size_t)max_eval * sizeof(uint16_t);
     return (b + 15) / 16 * 16;
 }

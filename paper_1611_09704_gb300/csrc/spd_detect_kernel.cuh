@@ -48,6 +48,7 @@ namespace spd {
 namespace {
 
 constexpr int kPad = 20;             // shared words per 16 positions
+constexpr int kMaxLevel = 5;         // sparse max table: windows up to 2^5 blocks
 constexpr int kWaitLimit = 1 << 22;  // bounded spin on a bulk copy (seconds)
 
 __device__ __forceinline__ int padr(int p) { return (p & 15) + kPad * (p >> 4); }
@@ -535,22 +536,70 @@ __device__ void build_stats(const float *s_y, float *s_g, float *s_bs, float *s_
 }
 
 // Per-range constants in shared memory: 1/sigma_w per eval index, the width
-// of each eval index, and (candidate search) the largest 1/sigma_w per group.
+// of each eval index, and (candidate search) per group the blocks its bound
+// looks at: the prefix maxima over blocks [t + a, t + b] of a unit t, read as
+// the maximum of two windows of 2^k blocks, [t + a, ...) and [t + bk, ...),
+// of the sparse max table (k = -1: a plain loop, for spans over 64 blocks),
+// with the group's largest 1/sigma_w.  *s_kmax = the highest level any group
+// reads.
 __device__ __forceinline__ void load_range_consts(const RangeDesc &rd, int entry, float *s_inv,
-                                                  uint16_t *s_ew, float *s_ginv, bool ginv) {
+                                                  uint16_t *s_ew, int4 *s_gb, int *s_kmax,
+                                                  bool bounds) {
     const RangeProg &rp = rd.prog;
     for (int q = threadIdx.x; q < rp.n_eval; q += kThreads)
         s_inv[q] = rd.inv_tab[(int64_t)entry * rp.n_eval + q];
+    if (threadIdx.x == 0) *s_kmax = 0;
+    __syncthreads();
     for (int gi = threadIdx.x; gi < rp.n_groups; gi += kThreads) {
         const Group g = rp.groups[gi];
         const int d = (g.flags & kGroupCoarse) ? rp.G : 1;
         float mxv = 0.f;
         for (int c = 0; c < g.count; ++c) {
             s_ew[g.widx0 + c] = (uint16_t)(g.off + (c + 1) * d);
-            if (ginv) mxv = fmaxf(mxv, rd.inv_tab[(int64_t)entry * rp.n_eval + g.widx0 + c]);
+            if (bounds) mxv = fmaxf(mxv, rd.inv_tab[(int64_t)entry * rp.n_eval + g.widx0 + c]);
         }
-        if (ginv) s_ginv[gi] = mxv;
+        if (bounds) {
+            const int a = (g.off + d) >> 4, b = (15 + g.off + g.count * d) >> 4;
+            const int len = b - a + 1;
+            int k = -1, bk = b;
+            if (len <= 2 << kMaxLevel) {
+                k = 31 - __clz(len);
+                if (k > kMaxLevel) k = kMaxLevel;
+                bk = b - (1 << k) + 1;
+                atomicMax(s_kmax, k);
+            }
+            s_gb[gi] = make_int4(a, bk, k, __float_as_int(mxv));
+        }
     }
+}
+
+// Sparse max table of the block prefix maxima: level k (1 <= k <= kmax)
+// holds the maximum of s_mx over blocks [c, c + 2^k) (fewer past the end).
+// Starts and ends with a barrier.
+__device__ __forceinline__ void build_max_table(const float *s_mx, float *s_st, int R, int RM,
+                                                int kmax) {
+    __syncthreads();
+    const int k3 = kmax < 3 ? kmax : 3;
+    for (int c = threadIdx.x; c < R; c += kThreads) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            v[j] = (j < (1 << k3) && c + j < R) ? s_mx[c + j] : -INFINITY;
+        const float m1 = fmaxf(v[0], v[1]);
+        const float m2 = fmaxf(m1, fmaxf(v[2], v[3]));
+        const float m3 = fmaxf(m2, fmaxf(fmaxf(v[4], v[5]), fmaxf(v[6], v[7])));
+        s_st[c] = m1;
+        if (k3 >= 2) s_st[RM + c] = m2;
+        if (k3 >= 3) s_st[2 * RM + c] = m3;
+    }
+    for (int k = 4; k <= kmax; ++k) {
+        __syncthreads();
+        const float *lo = s_st + (k - 2) * RM;
+        const int h = 1 << (k - 1);
+        for (int c = threadIdx.x; c < R; c += kThreads)
+            s_st[(k - 1) * RM + c] = fmaxf(lo[c], c + h < R ? lo[c + h] : -INFINITY);
+    }
+    __syncthreads();
 }
 
 template <int DT, int G, bool PLANE, bool MG>
@@ -565,9 +614,12 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
     float *s_bs = s_y + (G > 1 ? 2 : 1) * kPad * RM;
     float *s_mx = s_bs + RM;
     float *s_mn = s_mx + RM;
-    float *s_inv = s_mn + RM;
-    float *s_ginv = s_inv + L.max_eval;
-    uint16_t *s_ew = reinterpret_cast<uint16_t *>(s_ginv + kMaxCodeGroups);
+    float *s_st = s_mn + RM;                       // kMaxLevel levels of RM
+    float *s_inv = s_st + kMaxLevel * RM;
+    int4 *s_gb = reinterpret_cast<int4 *>(
+        (reinterpret_cast<uintptr_t>(s_inv + L.max_eval) + 15) & ~(uintptr_t)15);
+    uint16_t *s_ew = reinterpret_cast<uint16_t *>(s_gb + kMaxCodeGroups);
+    __shared__ int s_kmax;
     __shared__ int s_wsum[kThreads / 32];
     __shared__ unsigned long long s_base;
     __shared__ float s_wt[3 * (kThreads / 32) + 3 * kThreads];
@@ -626,10 +678,11 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         const T *rowp = static_cast<const T *>(rd.data) + row * rd.stride;
 
         if (tma) {
-            const bool ok = mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
-            // the whole CTA takes the same decision: if the copy did not land in
-            // time for any thread, report it, give the copy (the only one in
-            // flight) one more bounded wait, and leave
+            // thread 0 waits for the copy; the barrier then orders every
+            // thread's reads after it.  If the copy did not land in time the
+            // whole CTA reports it, gives the copy (the only one in flight)
+            // one more bounded wait, and leaves.
+            const bool ok = tid != 0 || mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     if (L.result) atomicExch(&L.result->status, (int)SPD_ERR_TIMEOUT);
@@ -651,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         if (!deg) {
             const int64_t nk = ((int64_t)ri << 32) | (uint32_t)entry;
             if (nk != key) {
-                load_range_consts(rd, entry, s_inv, s_ew, s_ginv, !PLANE);
+                load_range_consts(rd, entry, s_inv, s_ew, s_gb, &s_kmax, !PLANE);
                 key = nk;
             }
             // Stage centred samples; -inf past the row end and past the window.
@@ -697,6 +750,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         }
 
         build_stats<G>(s_y, s_g, s_bs, s_mx, s_mn, s_wt, R);   // ends with a barrier
+        if (!PLANE && s_kmax > 0) build_max_table(s_mx, s_st, R, RM, s_kmax);
 
         const float *sy_t = s_y + kPad * tid;
         const float *sg_t = s_g + kPad * tid;
@@ -790,19 +844,23 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         MaxSink mk;
         float minbest = -INFINITY;   // smallest current best of the 16 samples
         for (int gi = rp.n_groups - 1; gi >= 0; --gi) {
-            const Group g = rp.groups[gi];
-            const int d = group_step<G>(g);
             // upper bound over the thread's 16 samples and the group's widths
-            const int jb0 = tid + ((g.off + d) >> 4);
-            const int jb1 = tid + ((15 + g.off + g.count * d) >> 4);
-            float rmax = -INFINITY;
-            for (int jb = jb0; jb <= jb1; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
+            const int4 gb = s_gb[gi];
+            float rmax;
+            if (gb.z >= 0) {
+                const float *lv = gb.z ? s_st + (gb.z - 1) * RM : s_mx;
+                rmax = fmaxf(lv[tid + gb.x], lv[tid + gb.y]);
+            } else {
+                rmax = -INFINITY;
+                for (int jb = tid + gb.x; jb <= tid + gb.y; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
+            }
             const float lim = fmaxf(thr, minbest);
             const float ub = __fsub_rn(rmax, minC);
             const float slack = 1e-5f * (fabsf(rmax) + fabsf(minC)) + 1e-30f;
-            const float bound = ub > 0.f ? (ub + slack) * s_ginv[gi] * 1.00001f : 0.f;
+            const float bound = ub > 0.f ? (ub + slack) * __int_as_float(gb.w) * 1.00001f : 0.f;
             // a NaN bound (window past the row end) falls through to evaluation
             if (bound + 1e-5f * fabsf(lim) < lim) continue;
+            const Group g = rp.groups[gi];
             mk.reset();
             group_start(B, s_y, s_bs, tid, g.off);
             run_group<G>(B, mk, sy_t, sg_t, g, s_inv);
