@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["spd", "reference"], default="spd")
     ap.add_argument("--n-dm", type=int, default=4096)
     ap.add_argument("--n-samp", type=int, default=524288)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512)
@@ -278,7 +278,9 @@ def run_spd(a, rank, world, local):
         total_ms = float(t.item())
     ms_step = total_ms / a.steps
     value = world * n / (ms_step / 1e3)
-    e2e_line = None if a.no_e2e else e2e(ss, x, count, a.e2e_steps, n, world, dev)
+    e2e_line = None
+    if not a.no_e2e:
+        e2e_line = e2e(x, count, a.e2e_steps, n, world, rank, dev)
     if rank != 0:
         return 0
 
@@ -315,43 +317,51 @@ def run_spd(a, rank, world, local):
     return 0
 
 
-def e2e(ss, x, count, steps, n, world, dev):
-    """The sharded search from pinned host memory: H2D of the rank's rows, the
-    MSD exchange and the search, D2H of the count and of every candidate
-    record, per step; the slowest rank's time."""
+def e2e(x, count, steps, n, world, rank, dev):
+    """Planes searched from page-locked host memory through PlanePipeline:
+    every step copies its plane in, runs the sharded search and copies its
+    count and every candidate record out; two planes in flight overlap one
+    plane's copy out with the next one's copy in and search.  Whole-run time
+    (fill and drain included) / steps, slowest rank."""
     import torch
     import torch.distributed as dist
+
+    from paper_1611_09704_gb300.pipeline import PlanePipeline
     xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
     xh.copy_(x)
-    ch = torch.empty((max(count, 1), 4), dtype=torch.int32, pin_memory=True)
-    rh = torch.empty(16, dtype=torch.uint8, pin_memory=True)
-    times, d2h = [], []
-    for k in range(steps + 1):
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x.copy_(xh, non_blocking=True)
-        ss.run()
-        rh.copy_(ss.result, non_blocking=True)
-        torch.cuda.synchronize()
-        c = int(rh[:8].numpy().view("<u8")[0])
-        m = min(c, ss.capacity, ch.shape[0])
-        ch[:m].copy_(ss.out[:m], non_blocking=True)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if k:
-            times.append(dt)
-            d2h.append(16 + 16 * m)
-    t = sum(times) / len(times)
+    n_dm, n_samp = x.shape
+    cap = int(n * 0.45) + 1024
+    pp = PlanePipeline(n_dm, n_samp, WIDTHS, THRESHOLD, cap, dtype=x.dtype, depth=2, device=dev,
+                       dm_offset=rank * n_dm, host_capacity=count + (count >> 4) + 1024)
+    # one untimed plane (lazy set-up, page-in of the host buffers)
+    r = pp.collect(pp.submit(xh))
+    if r[0] != count:
+        raise RuntimeError(f"pipeline count {r[0]} != {count}")
+    d2h = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = [pp.submit(xh) for _ in range(min(2, steps))]
+    for k in range(steps):
+        c, st, recs = pp.collect(tickets[k])
+        if st != 0:
+            raise RuntimeError(f"pipeline status {st}")
+        d2h.append(16 + 16 * recs.shape[0])
+        if k + 2 < steps:
+            tickets.append(pp.submit(xh))
+    t = (time.perf_counter() - t0) / steps
     if world > 1:
         tt = torch.tensor([t], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
+    del pp
+    torch.cuda.empty_cache()
     return {"value": world * n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
             "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3,
-            "api": "ShardedSearch over the C ABI (shard partial, merge, detect) with pinned "
-                   "host buffers"}
+            "steps": steps,
+            "api": "PlanePipeline (sharded search over the C ABI) from page-locked host "
+                   "memory, 2 planes in flight"}
 
 
 def timed(step, steps, warmup, clocks_dev):
