@@ -53,12 +53,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
-    ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched", "serving"],
+    ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched", "serving",
+                                           "decimated"],
                     default="ska",
                     help="ska: the SKA-like FP32 chunk (default, the headline); plain: 64 x 65536 "
                          "FP32 noise + top-hats; precision: the SKA-like chunk stored as FP16 / "
                          "BF16 with Eq. 5; batched: four decimated DM ranges in one launch; "
-                         "serving: 16 beams of FP16 chunks streamed with continuous batching")
+                         "serving: 16 beams of FP16 chunks streamed with continuous batching; "
+                         "decimated: widths to 512 by decimation in time vs the plain search")
     ap.add_argument("--beams", type=int, default=16)
     ap.add_argument("--chunks-per-beam", type=int, default=3)
     ap.add_argument("--slots", type=int, default=4)
@@ -501,6 +503,43 @@ def run_other(a):
         return 0
     if a.workload == "serving":
         return run_serving(a, spd, synth, line, dev)
+    if a.workload == "decimated":
+        n_dm, n_samp = 2048, 524288
+        sp = synth.ska_like(n_dm, n_samp, n_pulses=200, mean=0.0, sd=1.0, drift_amp=0.0,
+                            fwhm_range=(1.0, 400.0), device=dev, seed=1611_6)
+        x = sp.data
+        n = n_dm * n_samp
+        levels = [(0, list(range(1, 33)))] + [(l, list(range(17, 33))) for l in range(1, 5)]
+        cap = 1 << 24
+        out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+        res = torch.zeros(16, dtype=torch.uint8, device=dev)
+        msd = torch.empty(len(levels) * 40, dtype=torch.uint8, device=dev)
+        ws = torch.empty(spd.search_decimated_workspace_bytes(x, levels), dtype=torch.uint8,
+                         device=dev)
+        step = lambda: spd.search_decimated(x, levels, THRESHOLD, cap, out=out, result=res,
+                                            msd_out=msd, workspace=ws)
+        ms, clocks = timed(step, a.steps, a.warmup, 0)
+        cnt = spd.read_result(res)[0]
+        plain_w = list(range(1, 513))
+        ws2 = torch.empty(spd.search_workspace_bytes(x, plain_w, THRESHOLD), dtype=torch.uint8,
+                          device=dev)
+        step2 = lambda: spd.search(x, plain_w, THRESHOLD, cap, out=out, result=res,
+                                   msd_out=msd[:40], workspace=ws2)
+        ms2, _ = timed(step2, max(3, a.steps // 4), 3, 0)
+        cnt2 = spd.read_result(res)[0]
+        line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    candidates_per_step=cnt, gpu_launches=(4 + 5 * len(levels)) * a.steps,
+                    plain_search={"widths": "1..512", "ms_per_step": ms2, "value": n / (ms2 / 1e3),
+                                  "candidates": cnt2},
+                    speedup_vs_plain=ms2 / ms,
+                    realtime_factor=n_samp * SAMPLE_TIME_S / (ms / 1e3),
+                    config={"workload": f"{n_dm} DM x {n_samp} FP32 N(0,1) + 200 Gaussian pulses "
+                                        "(FWHM 1..400); levels 0: widths 1..32, 1-4: 17..32 "
+                                        "level samples (native to 512), each level its own "
+                                        "MSD; f_T 7",
+                            "l2": "inputs larger than L2"})
+        print(json.dumps(line))
+        return 0
     raise SystemExit(f"unknown workload {a.workload}")
 
 

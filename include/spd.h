@@ -251,6 +251,16 @@ spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int
                                     spd_candidate *out, int64_t capacity,
                                     spd_result *result_dev, void *stream);
 
+/* Step (d) as the thresholding of Sec. 2.4 writes it, on the plane: in place,
+ * snr[dm][t] keeps its value where snr >= threshold and becomes 0 elsewhere
+ * (a NaN SNR, from a degenerate MSD, is not >= threshold and becomes 0);
+ * width[dm][t] (may be NULL) keeps the width where the SNR is kept, else 0.
+ * The kept entries are exactly the records of spd_threshold_candidates.
+ * snr, width: device planes [n_dm][stride].  Errors: SPD_ERR_INVALID_ARG,
+ * SPD_ERR_CUDA. */
+spd_status spd_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, int64_t n_samp,
+                               int64_t stride, float threshold, void *stream);
+
 /* Bytes of device workspace spd_detect / spd_search need. */
 size_t spd_detect_workspace_bytes(const spd_plane *plane, const spd_search_params *params);
 size_t spd_search_workspace_bytes(const spd_plane *plane, const spd_search_params *params);
@@ -382,6 +392,33 @@ spd_status spd_stream_flush(spd_stream_info *info, void *state_dev,
                             const spd_search_params *params, spd_candidate *out,
                             int64_t capacity, spd_result *result_dev, void *workspace,
                             size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------- decimation in time
+ * Wide boxcars on data decimated in time, which Sec. 3 names as the way to
+ * widen the search; the paper gives no details, so this is this library's
+ * scheme.  Level l searches the series x_l[j] = x[2^l j] + ... + x[2^l j +
+ * 2^l - 1] (complete groups only, FP32) with its own listed widths (in level
+ * samples) and its own measured MSD (Sec. 2.1 on x_l, global scope, Eq. 4),
+ * thresholded like the plain search.  A level-l boxcar of w samples at j is
+ * the plain B_{w 2^l}(j 2^l), so level l evaluates native widths w 2^l at
+ * starts that are multiples of 2^l only: a variant of the plain search, not
+ * equal to it.  Records carry native units: sample j 2^l, width w 2^l; the
+ * levels' native widths must ascend strictly from level to level, so a
+ * record's width tells its level.  msd_out_dev (optional): one spd_msd_stats
+ * per level.  Errors: as spd_search_batched. */
+#define SPD_MAX_LEVELS 8
+typedef struct {
+    int32_t level;           /* 0 .. 12, strictly ascending over the array */
+    int32_t n_widths;
+    const int32_t *widths;   /* host, ascending, in samples of the level */
+} spd_level;
+
+size_t spd_search_decimated_workspace_bytes(const spd_plane *plane, const spd_level *levels,
+                                            int32_t n_levels);
+spd_status spd_search_decimated(const spd_plane *plane, const spd_level *levels, int32_t n_levels,
+                                float threshold, spd_candidate *out, int64_t capacity,
+                                spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                                void *workspace, size_t workspace_bytes, void *stream);
 
 /* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
  * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */

@@ -18,6 +18,8 @@ numpy arrays.  Function by function:
 - :func:`search` -- the four steps in order.
 - :func:`stream_replay` -- the same search over a stream delivered in chunks
   (running MSD, held-back starts, end-of-stream flush).
+- :func:`decimate`, :func:`search_decimated` -- boxcars on data decimated in
+  time (Sec. 3), level by level.
 """
 from __future__ import annotations
 
@@ -72,7 +74,7 @@ def _load():
     lib.oracle_boxcar_sums.argtypes = [P, I32, I64, I64, I64, P, P, I32, P]
     lib.oracle_boxcar_sums.restype = I32
     lib.oracle_boxcar_snr.argtypes = [P, I32, I64, I64, I64, P, P, I32, P, P, P, P,
-                                      I32, I64, I64, P, P]
+                                      I32, I64, I64, P, P, I32]
     lib.oracle_boxcar_snr.restype = I32
     lib.oracle_threshold.argtypes = [P, P, I64, I64, I64, D, P, P, P, P, I64]
     lib.oracle_threshold.restype = I64
@@ -229,11 +231,12 @@ def boxcar_sums(plane, w: int) -> np.ndarray:
 
 
 def boxcar_snr(plane, mean, sd, sigma_tab, widths, scope: int = SCOPE_GLOBAL,
-               rows: tuple[int, int] | None = None):
+               rows: tuple[int, int] | None = None, start_w1: bool = True):
     """Algorithm 1: per-sample (highest SNR, winning width) for rows [r0, r1).
 
     mean, sd: arrays of length 1 (global scope) or n_dm (per row);
-    sigma_tab: [entries, n_widths] sigma_w."""
+    sigma_tab: [entries, n_widths] sigma_w.  start_w1=False evaluates only the
+    listed widths (no width-1 start; -inf and width 0 where none fits)."""
     p = as_plane(plane)
     w = np.ascontiguousarray(widths, dtype=np.int32)
     r0, r1 = rows if rows is not None else (0, p.n_dm)
@@ -243,7 +246,8 @@ def boxcar_snr(plane, mean, sd, sigma_tab, widths, scope: int = SCOPE_GLOBAL,
     best = np.empty((r1 - r0, p.n_samp))
     win = np.empty((r1 - r0, p.n_samp), dtype=np.int32)
     rc = _load().oracle_boxcar_snr(*p.args(), scope, _ptr(mean), _ptr(sd), _ptr(tab),
-                                   _ptr(w), w.size, r0, r1, _ptr(best), _ptr(win))
+                                   _ptr(w), w.size, r0, r1, _ptr(best), _ptr(win),
+                                   1 if start_w1 else 0)
     if rc:
         raise ValueError(f"oracle_boxcar_snr rc={rc}")
     return best, win
@@ -279,6 +283,14 @@ def threshold(best, width, thr: float, row0: int = 0):
     return out
 
 
+def threshold_plane(best, width, thr: float):
+    """Sec. 2.4's thresholding on the plane: a value is kept where it is >= thr
+    and becomes 0 below (NaN, never >= thr, becomes 0); widths likewise."""
+    best = np.asarray(best, dtype=np.float64)
+    keep = best >= thr
+    return np.where(keep, best, 0.0), np.where(keep, np.asarray(width), 0)
+
+
 # ------------------------------------------------------------ whole path
 
 def msd_and_sigma(plane, widths, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=0):
@@ -297,11 +309,11 @@ def msd_and_sigma(plane, widths, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nma
 
 
 def search(plane, widths, thr, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=0,
-           rows=None):
+           rows=None, start_w1=True):
     """The four steps in the paper's order; returns (candidates, best, width, msd)."""
     p = as_plane(plane)
     mean, sd, sdn, tab = msd_and_sigma(p, widths, sigma_mode, scope, nmax)
-    best, win = boxcar_snr(p, mean, sd, tab, widths, scope, rows)
+    best, win = boxcar_snr(p, mean, sd, tab, widths, scope, rows, start_w1)
     r0 = rows[0] if rows else 0
     cands = threshold(best, win, thr, row0=r0)
     return cands, best, win, (mean, sd, sdn, tab)
@@ -354,3 +366,46 @@ def stream_replay(chunks, widths, thr, scope=SCOPE_GLOBAL, dtype="f32", scale=No
         emitted = hi
     out.append(search_range(np.concatenate(parts, axis=1) if parts else None, emitted, n))
     return out
+
+
+# ------------------------------------------------------- decimation in time
+
+def decimate(plane, level: int) -> np.ndarray:
+    """x_l[j] = x[2^l j] + ... + x[2^l j + 2^l - 1] of the dequantised values,
+    in FP64, complete groups only: [n_dm, n_samp >> level]."""
+    p = as_plane(plane)
+    x = p.values()
+    m = 1 << level
+    n = p.n_samp >> level
+    return x[:, :n * m].reshape(p.n_dm, n, m).sum(axis=2)
+
+
+def search_decimated(plane, levels, thr):
+    """Sec. 3 names decimation in time as the way to widen the boxcars and
+    gives no details; the reading here: level l searches its decimated series
+    (rounded to FP32, the precision a search takes its samples in) with its
+    listed widths (level samples), its own MSD (global scope, Eq. 4) and the
+    threshold, as one plain search -- except that a level above 0 evaluates
+    only its listed widths: Algorithm 1's width-1 start belongs to the native
+    series.  Records are reported in native units (sample j 2^l, width w 2^l)
+    with the level.  Returns the records of every level, concatenated in level
+    order, and per level (mean, sd)."""
+    out, msds = [], []
+    for level, widths in levels:
+        xl = decimate(plane, level)
+        if xl.shape[1] == 0:
+            msds.append((np.nan, np.nan))
+            continue
+        start_w1 = level == 0 or widths[0] == 1
+        cands, best, win, (mean, sd, _, _) = search(xl.astype(np.float32), widths, thr,
+                                                    start_w1=start_w1)
+        c = np.empty(len(cands), dtype=[("dm", np.int32), ("sample", np.int64),
+                                        ("snr", np.float64), ("width", np.int64),
+                                        ("level", np.int32)])
+        c["dm"], c["snr"] = cands["dm"], cands["snr"]
+        c["sample"] = cands["sample"].astype(np.int64) << level
+        c["width"] = cands["width"].astype(np.int64) << level
+        c["level"] = level
+        out.append(c)
+        msds.append((float(mean[0]), float(sd[0])))
+    return (np.concatenate(out) if out else np.empty(0)), msds

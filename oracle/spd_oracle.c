@@ -353,7 +353,8 @@ int oracle_boxcar_snr(const void *data, int dtype, int64_t n_dm, int64_t n_samp,
                       int64_t stride, const float *scale, const float *offset,
                       int scope, const double *mean, const double *sd,
                       const double *sigma_tab, const int32_t *widths, int n_widths,
-                      int64_t row0, int64_t row1, double *best_out, int32_t *width_out)
+                      int64_t row0, int64_t row1, double *best_out, int32_t *width_out,
+                      int start_w1)
 {
     if (row0 < 0 || row1 > n_dm || row0 > row1 || n_widths < 0) return -1;
     for (int k = 1; k < n_widths; ++k)
@@ -372,8 +373,10 @@ int oracle_boxcar_snr(const void *data, int dtype, int64_t n_dm, int64_t n_samp,
             for (int64_t t = 0; t < n_samp; ++t)
                 x[t] = sample_value(data, dtype, stride, scale, offset, r, t);
             for (int64_t i = 0; i < n_samp; ++i) {
-                double best = (x[i] - mu) / sg;
-                int32_t W = 1;
+                /* Algorithm 1 starts from width 1; start_w1 = 0 evaluates the
+                   listed widths only (best -inf, width 0 when none fits) */
+                double best = start_w1 ? (x[i] - mu) / sg : -INFINITY;
+                int32_t W = start_w1 ? 1 : 0;
                 double B = 0.0;
                 int64_t grown = 0;
                 for (int k = 0; k < n_widths; ++k) {

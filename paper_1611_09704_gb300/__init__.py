@@ -10,5 +10,6 @@ from .binding import (  # noqa: F401
     BF16, F16, F32, MSD_GLOBAL, MSD_PER_ROW, SIGMA_LINEAR, SIGMA_LINEAR_EXCESS, SIGMA_SQRTN,
     CAND_DTYPE, MSD_DTYPE, Plane, SpdError, boxcar_snr, boxcar_sums, candidates_to_numpy,
     detect, load, msd, msd_to_numpy, read_result, search, search_workspace_bytes,
-    threshold_candidates, widths_to_numpy, RangeSpec, BatchedSearch, search_batched,
-    search_batched_workspace_bytes, SpdTuning, BeamStream)
+    threshold_candidates, threshold_plane, widths_to_numpy, RangeSpec, BatchedSearch, search_batched,
+    search_batched_workspace_bytes, SpdTuning, BeamStream, search_decimated,
+    search_decimated_workspace_bytes)

@@ -75,6 +75,11 @@ class SpdStreamInfo(ctypes.Structure):
                 ("has_offset", ctypes.c_int32)]
 
 
+class SpdLevel(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("n_widths", ctypes.c_int32),
+                ("widths", ctypes.POINTER(ctypes.c_int32))]
+
+
 class SpdMsdPart(ctypes.Structure):
     _fields_ = [("n", ctypes.c_double), ("T", ctypes.c_double), ("S", ctypes.c_double),
                 ("lo", ctypes.c_double), ("hi", ctypes.c_double)]
@@ -98,7 +103,8 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_stream_state_bytes", "spd_stream_workspace_bytes", "spd_stream_reset",
            "spd_stream_push", "spd_stream_chunk_view", "spd_stream_flush",
            "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
-           "spd_sd_nmax_merge_partials"]
+           "spd_sd_nmax_merge_partials", "spd_threshold_plane",
+           "spd_search_decimated_workspace_bytes", "spd_search_decimated"]
 
 
 class SpdError(RuntimeError):
@@ -163,6 +169,13 @@ def load(path: str | None = None):
     lib.spd_search_batched_workspace_bytes.restype = SZ
     lib.spd_search_batched.argtypes = [pr, I32, pt, P, I64, P, P, P, SZ, P]
     lib.spd_search_batched.restype = I32
+    plv = ctypes.POINTER(SpdLevel)
+    lib.spd_search_decimated_workspace_bytes.argtypes = [pp, plv, I32]
+    lib.spd_search_decimated_workspace_bytes.restype = SZ
+    lib.spd_search_decimated.argtypes = [pp, plv, I32, F, P, I64, P, P, P, SZ, P]
+    lib.spd_search_decimated.restype = I32
+    lib.spd_threshold_plane.argtypes = [P, P, I64, I64, I64, F, P]
+    lib.spd_threshold_plane.restype = I32
     lib.spd_msd_shard_partial.argtypes = [pp, P, P, SZ, P]
     lib.spd_msd_shard_partial.restype = I32
     lib.spd_msd_merge_partials.argtypes = [P, I32, P, P]
@@ -366,6 +379,18 @@ def threshold_candidates(snr, width, threshold, capacity, *, n_samp=None, stream
     return out, result
 
 
+def threshold_plane(snr, width, threshold, *, n_samp=None, stream=None):
+    """spd_threshold_plane, in place: SNR (and width) kept where SNR >=
+    threshold, 0 elsewhere (Sec. 2.4)."""
+    n_samp = snr.shape[1] if n_samp is None else n_samp
+    if width is not None and width.stride(0) != snr.stride(0):
+        raise ValueError("snr and width planes must share a row stride")
+    _check(load().spd_threshold_plane(_ptr(snr), _ptr(width), snr.shape[0], int(n_samp),
+                                      snr.stride(0), float(threshold), _stream(stream)),
+           "spd_threshold_plane")
+    return snr, width
+
+
 def detect(x, msd_dev, widths, threshold, capacity, sigma_mode=SIGMA_SQRTN, scope=MSD_GLOBAL,
            nmax_sigma=0, *, stream=None, out=None, result=None, workspace=None, **kw):
     """spd_detect (steps b-d given the MSD): (records, result)."""
@@ -542,6 +567,51 @@ class BatchedSearch:
         else:
             self._call(None)
         return self.out, self.result
+
+
+# ------------------------------------------------------------- decimation
+
+def _levels(levels):
+    arr = (SpdLevel * len(levels))()
+    keep = []
+    for i, (lvl, widths) in enumerate(levels):
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        keep.append(w)
+        arr[i] = SpdLevel(int(lvl), w.size, w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return arr, keep
+
+
+def search_decimated_workspace_bytes(x, levels, **kw) -> int:
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    arr, keep = _levels(levels)
+    return int(load().spd_search_decimated_workspace_bytes(ctypes.byref(cp), arr, len(levels)))
+
+
+def search_decimated(x, levels, threshold, capacity, *, stream=None, out=None, result=None,
+                     msd_out=None, workspace=None, **kw):
+    """spd_search_decimated: levels = [(level, widths in level samples), ...];
+    returns (records in native units, result, msd of every level)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    dev = pl.data.device
+    arr, keep = _levels(levels)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 4), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    if msd_out is None:
+        msd_out = torch.empty(len(levels) * MSD_BYTES, dtype=torch.uint8, device=dev)
+    wsb = lib.spd_search_decimated_workspace_bytes(ctypes.byref(cp), arr, len(levels))
+    if wsb == 0:
+        raise SpdError(SPD_ERR_INVALID_ARG, "spd_search_decimated_workspace_bytes")
+    ws = workspace if workspace is not None else _workspace(wsb, dev)
+    _check(lib.spd_search_decimated(ctypes.byref(cp), arr, len(levels), float(threshold),
+                                    _ptr(out), int(capacity), _ptr(result), _ptr(msd_out),
+                                    _ptr(ws), ws.numel(), _stream(stream)),
+           "spd_search_decimated")
+    return out, result, msd_out
 
 
 # ---------------------------------------------------------------- streaming

@@ -209,7 +209,7 @@ int nmax_of(const spd_search_params *q) {
 // Constants kernel for one range: 1/sigma_w per entry and width, mean, flags.
 spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd_stats *msd_dev,
                         int scope, int sigma_mode, spd_result *result, void *ws,
-                        cudaStream_t st, RangeDesc &rd) {
+                        cudaStream_t st, RangeDesc &rd, int skip_w1 = 0) {
     const int64_t entries = entries_of(p, scope);
     const DetLayout L = det_layout(entries, prog.n_eval);
     char *base = static_cast<char *>(ws);
@@ -221,6 +221,7 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
     c.mu_tab = reinterpret_cast<float2 *>(base + L.mu_off);
     c.flags = reinterpret_cast<int32_t *>(base + L.flags_off);
     c.result = result;
+    c.skip_w1 = skip_w1;
     SPD_CK(launch_consts(c, prog, st));
 
     memset(&rd, 0, sizeof(rd));
@@ -240,6 +241,7 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
     rd.span = prog_span(prog);
     rd.n_emit = p->n_samp;
     rd.sample_base = 0;
+    rd.sample_shift = 0;
     rd.prog = prog;
     return SPD_OK;
 }
@@ -481,6 +483,18 @@ spd_status spd_boxcar_snr(const spd_plane *plane, const spd_msd_stats *msd_dev, 
                       static_cast<cudaStream_t>(stream));
 }
 
+spd_status spd_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, int64_t n_samp,
+                               int64_t stride, float threshold, void *stream) {
+    if (n_dm < 0 || n_samp < 0 || n_dm > INT32_MAX || n_samp > INT32_MAX) return SPD_ERR_INVALID_ARG;
+    if (n_dm == 0 || n_samp == 0) return SPD_OK;
+    if (!snr || stride < n_samp || !isfinite(threshold)) return SPD_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(snr) % 4 || reinterpret_cast<uintptr_t>(width) % 2)
+        return SPD_ERR_INVALID_ARG;
+    SPD_CK(launch_threshold_plane(snr, width, n_dm, n_samp, stride, threshold,
+                                  static_cast<cudaStream_t>(stream)));
+    return SPD_OK;
+}
+
 spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int64_t n_dm,
                                     int64_t n_samp, int64_t stride, float threshold,
                                     spd_candidate *out, int64_t capacity,
@@ -588,7 +602,6 @@ spd_status batch_plan(const spd_range *ranges, int n, const spd_tuning *tuning,
         const spd_range &r = ranges[i];
         SPD_TRY(check_plane(&r.plane));
         SPD_TRY(check_params(&r.params));
-        if (r.plane.dtype != ranges[0].plane.dtype) return SPD_ERR_INVALID_ARG;
         if (r.dm_offset < 0 || r.decimation < 0) return SPD_ERR_INVALID_ARG;
         SPD_TRY(compile_program(r.params.widths, r.params.n_widths, progs[i], scale));
         const int64_t entries = entries_of(&r.plane, r.params.msd_scope);
@@ -603,6 +616,11 @@ spd_status batch_plan(const spd_range *ranges, int n, const spd_tuning *tuning,
     L.total = off;
     return SPD_OK;
 }
+
+spd_status batched_impl(const spd_range *ranges, int32_t n_ranges, const spd_tuning *tuning,
+                        const int *shifts, spd_candidate *out, int64_t capacity,
+                        spd_result *result_dev, spd_msd_stats *msd_out_dev, void *workspace,
+                        size_t workspace_bytes, void *stream);
 
 }  // namespace
 
@@ -620,6 +638,20 @@ spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
                               const spd_tuning *tuning, spd_candidate *out, int64_t capacity,
                               spd_result *result_dev, spd_msd_stats *msd_out_dev,
                               void *workspace, size_t workspace_bytes, void *stream) {
+    return batched_impl(ranges, n_ranges, tuning, nullptr, out, capacity, result_dev,
+                        msd_out_dev, workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The batched search; shifts (NULL = none): per range, records carry
+// start << shift and width << shift.
+spd_status batched_impl(const spd_range *ranges, int32_t n_ranges, const spd_tuning *tuning,
+                        const int *shifts, spd_candidate *out, int64_t capacity,
+                        spd_result *result_dev, spd_msd_stats *msd_out_dev, void *workspace,
+                        size_t workspace_bytes, void *stream) {
     static thread_local RangeProg progs[kMaxRanges];
     BatchLayout L;
     SPD_TRY(batch_plan(ranges, n_ranges, tuning, progs, L));
@@ -643,14 +675,17 @@ spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
         if (plane_empty(&r.plane)) continue;
         SPD_TRY(spd_msd(&r.plane, r.params.msd_scope, nmax_of(&r.params), msd,
                         base + L.msd_off[i], L.msd_bytes[i], stream));
+        // a decimated level evaluates only its listed widths
+        const int skip_w1 = shifts && shifts[i] > 0 && r.params.widths[0] != 1;
         SPD_TRY(range_consts(&r.plane, progs[i], msd, r.params.msd_scope, r.params.sigma_mode,
-                             result_dev, base + L.det_off[i], st, rds[i]));
+                             result_dev, base + L.det_off[i], st, rds[i], skip_w1));
         rds[i].threshold = r.params.threshold;
         rds[i].dm_offset = r.dm_offset;
+        rds[i].sample_shift = shifts ? shifts[i] : 0;
         live[n_live++] = i;
     }
-    // (b, c, d): one persistent launch per class of ranges with equal G and
-    // equal bulk-copy eligibility
+    // (b, c, d): one persistent launch per class of ranges with equal G,
+    // storage type and bulk-copy eligibility
     bool done[kMaxRanges] = {false};
     for (int a = 0; a < n_live; ++a) {
         const int i = live[a];
@@ -659,15 +694,129 @@ spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
         int m = 0;
         for (int b = a; b < n_live; ++b) {
             const int j = live[b];
-            if (done[j] || rds[j].prog.G != rds[i].prog.G || rds[j].vec_ok != rds[i].vec_ok)
+            if (done[j] || rds[j].prog.G != rds[i].prog.G || rds[j].vec_ok != rds[i].vec_ok ||
+                ranges[j].plane.dtype != ranges[i].plane.dtype)
                 continue;
             grp[m++] = rds[j];
             done[j] = true;
         }
-        SPD_TRY(run_launch(grp, m, ranges[0].plane.dtype, out, capacity, result_dev, nullptr,
+        SPD_TRY(run_launch(grp, m, ranges[i].plane.dtype, out, capacity, result_dev, nullptr,
                            nullptr, 0, tuning ? tuning->ctas_per_sm : 0, st));
     }
     return SPD_OK;
+}
+
+// Decimated search: level planes (FP32, rows 16-byte aligned), then the
+// batched workspace of the levels' ranges.
+constexpr int kMaxDecLevel = 12;
+struct DecLayout {
+    int lmax;
+    int64_t n[kMaxDecLevel + 1], stride[kMaxDecLevel + 1];
+    size_t plane_off[kMaxDecLevel + 1];
+    size_t batch_off, batch_bytes, total;
+};
+
+spd_status dec_plan(const spd_plane *plane, const spd_level *levels, int32_t n_levels,
+                    float threshold, spd_range *ranges, int *shifts, DecLayout &D,
+                    char *ws_base) {
+    SPD_TRY(check_plane(plane));
+    if (!levels || n_levels < 1 || n_levels > SPD_MAX_LEVELS || !isfinite(threshold))
+        return SPD_ERR_INVALID_ARG;
+    int prev_level = -1, prev_wmax = 0;
+    for (int k = 0; k < n_levels; ++k) {
+        const spd_level &lv = levels[k];
+        if (lv.level <= prev_level || lv.level < 0 || lv.level > kMaxDecLevel) return SPD_ERR_INVALID_ARG;
+        if (!lv.widths || lv.n_widths < 1) return SPD_ERR_INVALID_ARG;
+        // native widths of the levels strictly ascending: a record's width
+        // tells its level
+        if (((int64_t)lv.widths[0] << lv.level) <= prev_wmax && k > 0) return SPD_ERR_INVALID_ARG;
+        prev_level = lv.level;
+        prev_wmax = (int)((int64_t)lv.widths[lv.n_widths - 1] << lv.level);
+    }
+    D.lmax = levels[n_levels - 1].level;
+    size_t off = 0;
+    D.n[0] = plane->n_samp;
+    D.stride[0] = plane->row_stride;
+    for (int l = 1; l <= D.lmax; ++l) {
+        D.n[l] = plane->n_samp >> l;
+        D.stride[l] = (D.n[l] + 7) / 8 * 8;
+        D.plane_off[l] = off;
+        off += align_up((size_t)plane->n_dm * D.stride[l] * sizeof(float));
+    }
+    for (int k = 0; k < n_levels; ++k) {
+        const int l = levels[k].level;
+        spd_range &r = ranges[k];
+        memset(&r, 0, sizeof(r));
+        if (l == 0) {
+            r.plane = *plane;
+        } else {
+            r.plane.data = ws_base ? ws_base + D.plane_off[l] : reinterpret_cast<void *>(256);
+            r.plane.dtype = SPD_F32;
+            r.plane.n_dm = plane->n_dm;
+            r.plane.n_samp = D.n[l];
+            r.plane.row_stride = D.stride[l];
+        }
+        r.params.widths = levels[k].widths;
+        r.params.n_widths = levels[k].n_widths;
+        r.params.threshold = threshold;
+        r.params.sigma_mode = SPD_SIGMA_SQRTN;
+        r.params.msd_scope = SPD_MSD_GLOBAL;
+        r.dm_offset = 0;
+        r.decimation = 1 << l;
+        shifts[k] = l;
+    }
+    RangeProg progs[kMaxRanges];
+    BatchLayout B;
+    SPD_TRY(batch_plan(ranges, n_levels, nullptr, progs, B));
+    D.batch_off = off;
+    D.batch_bytes = B.total;
+    D.total = off + align_up(B.total);
+    return SPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t spd_search_decimated_workspace_bytes(const spd_plane *plane, const spd_level *levels,
+                                            int32_t n_levels) {
+    spd_range ranges[SPD_MAX_LEVELS];
+    int shifts[SPD_MAX_LEVELS];
+    DecLayout D;
+    if (dec_plan(plane, levels, n_levels, 1.f, ranges, shifts, D, nullptr) != SPD_OK) return 0;
+    return D.total;
+}
+
+spd_status spd_search_decimated(const spd_plane *plane, const spd_level *levels, int32_t n_levels,
+                                float threshold, spd_candidate *out, int64_t capacity,
+                                spd_result *result_dev, spd_msd_stats *msd_out_dev,
+                                void *workspace, size_t workspace_bytes, void *stream) {
+    spd_range ranges[SPD_MAX_LEVELS];
+    int shifts[SPD_MAX_LEVELS];
+    DecLayout D;
+    char *base = static_cast<char *>(workspace);
+    SPD_TRY(dec_plan(plane, levels, n_levels, threshold, ranges, shifts, D, base));
+    SPD_TRY(check_ws(workspace, workspace_bytes, D.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // level l from level l - 1 (the input plane for l = 1)
+    for (int l = 1; l <= D.lmax; ++l) {
+        spd_plane src;
+        if (l == 1) {
+            src = *plane;
+        } else {
+            memset(&src, 0, sizeof(src));
+            src.data = base + D.plane_off[l - 1];
+            src.dtype = SPD_F32;
+            src.n_dm = plane->n_dm;
+            src.n_samp = D.n[l - 1];
+            src.row_stride = D.stride[l - 1];
+        }
+        if (!plane_empty(&src))
+            SPD_CK(launch_decimate2(src, reinterpret_cast<float *>(base + D.plane_off[l]), D.n[l],
+                                    D.stride[l], st));
+    }
+    return batched_impl(ranges, n_levels, nullptr, shifts, out, capacity, result_dev, msd_out_dev,
+                        base + D.batch_off, D.batch_bytes, stream);
 }
 
 }  // extern "C"

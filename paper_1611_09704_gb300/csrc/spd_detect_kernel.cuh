@@ -945,9 +945,10 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
                     if (idx < (unsigned long long)L.capacity) {
                         int4 rec;
                         rec.x = rd.dm_offset + (int)row;
-                        rec.y = (int)(rd.sample_base + i0 + q);
+                        rec.y = (int)(rd.sample_base + ((i0 + q) << rd.sample_shift));
                         rec.z = __float_as_int(trunc17(rk.best[q]));
-                        rec.w = (int)s_ew[base - (int)(__float_as_uint(rk.best[q]) & 63u)];
+                        rec.w = (int)s_ew[base - (int)(__float_as_uint(rk.best[q]) & 63u)]
+                                << rd.sample_shift;
                         reinterpret_cast<int4 *>(L.out)[idx] = rec;
                     }
                 }

@@ -122,6 +122,8 @@ struct RangeDesc {
     float threshold;
     int64_t n_emit;             // only starts < n_emit become candidates (n_samp normally)
     int64_t sample_base;        // added to the start sample in candidate records
+    int32_t sample_shift;       // records carry start << shift and width << shift
+    int32_t reserved0;
     RangeProg prog;
 };
 
@@ -151,6 +153,7 @@ struct ConstArgs {
     float2 *mu_tab;
     int32_t *flags;
     spd_result *result;   // may be null: zeroed count/status when given
+    int skip_w1;          // eval index 0 (the width-1 start) takes no part: 1/sigma = NaN
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -175,6 +178,11 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
                         spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
                           size_t smem, int ctas_per_sm, cudaStream_t s);
+// x[2j] + x[2j+1] of a plane (dequantised) into an FP32 plane, j < n_out.
+cudaError_t launch_decimate2(const spd_plane &p, float *dst, int64_t n_out, int64_t dst_stride,
+                             cudaStream_t s);
+cudaError_t launch_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, int64_t n_samp,
+                                   int64_t stride, float thr, cudaStream_t s);
 cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,
                              int64_t n_samp, int64_t stride, float thr, spd_candidate *out,
                              int64_t capacity, spd_result *result, cudaStream_t s);

@@ -128,6 +128,125 @@ __global__ void boxcar_sums_kernel(const spd_plane p, int w, float *out, int64_t
 
 }  // namespace
 
+// Thresholding of Sec. 2.4 on the plane, in place: 8 samples per thread,
+// 128-bit accesses where the row allows.
+__global__ void __launch_bounds__(256) threshold_plane_kernel(float *snr, uint16_t *width,
+                                                              int64_t n_samp, int64_t stride,
+                                                              float thr) {
+    const int64_t row = blockIdx.y;
+    const int64_t i0 = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 8;
+    if (i0 >= n_samp) return;
+    float *sp = snr + row * stride;
+    uint16_t *wp = width ? width + row * stride : nullptr;
+    const bool vec = i0 + 8 <= n_samp && ((reinterpret_cast<uintptr_t>(sp + i0) & 15) == 0) &&
+                     (!wp || (reinterpret_cast<uintptr_t>(wp + i0) & 15) == 0);
+    if (vec) {
+        float4 a = reinterpret_cast<float4 *>(sp + i0)[0];
+        float4 b = reinterpret_cast<float4 *>(sp + i0)[1];
+        const bool k[8] = {a.x >= thr, a.y >= thr, a.z >= thr, a.w >= thr,
+                           b.x >= thr, b.y >= thr, b.z >= thr, b.w >= thr};
+        a.x = k[0] ? a.x : 0.f; a.y = k[1] ? a.y : 0.f; a.z = k[2] ? a.z : 0.f;
+        a.w = k[3] ? a.w : 0.f; b.x = k[4] ? b.x : 0.f; b.y = k[5] ? b.y : 0.f;
+        b.z = k[6] ? b.z : 0.f; b.w = k[7] ? b.w : 0.f;
+        reinterpret_cast<float4 *>(sp + i0)[0] = a;
+        reinterpret_cast<float4 *>(sp + i0)[1] = b;
+        if (wp) {
+            uint4 u = reinterpret_cast<uint4 *>(wp + i0)[0];
+            uint32_t *uw = reinterpret_cast<uint32_t *>(&u);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t lo = k[2 * q] ? (uw[q] & 0xffffu) : 0u;
+                const uint32_t hi = k[2 * q + 1] ? (uw[q] & 0xffff0000u) : 0u;
+                uw[q] = lo | hi;
+            }
+            reinterpret_cast<uint4 *>(wp + i0)[0] = u;
+        }
+        return;
+    }
+    for (int q = 0; q < 8 && i0 + q < n_samp; ++q) {
+        const bool keep = sp[i0 + q] >= thr;
+        if (!keep) {
+            sp[i0 + q] = 0.f;
+            if (wp) wp[i0 + q] = 0;
+        }
+    }
+}
+
+cudaError_t launch_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, int64_t n_samp,
+                                   int64_t stride, float thr, cudaStream_t s) {
+    if (n_dm <= 0 || n_samp <= 0) return cudaSuccess;
+    const int64_t per = 256 * 8;
+    int64_t y = n_dm;
+    for (int64_t r0 = 0; r0 < n_dm; r0 += 65535) {   // grid.y limit
+        y = n_dm - r0 < 65535 ? n_dm - r0 : 65535;
+        const dim3 grid((unsigned)((n_samp + per - 1) / per), (unsigned)y);
+        threshold_plane_kernel<<<grid, 256, 0, s>>>(snr + r0 * stride,
+                                                    width ? width + r0 * stride : nullptr,
+                                                    n_samp, stride, thr);
+    }
+    return cudaGetLastError();
+}
+
+// Decimation in time by 2: dst[r][j] = x[r][2j] + x[r][2j+1] in FP32 (x the
+// dequantised source), for j < n_out.  Four outputs per thread.
+template <int DT>
+__global__ void __launch_bounds__(256) decimate2_kernel(const typename Elem<DT>::T *src,
+                                                        int64_t src_stride, const float *scale,
+                                                        const float *offset, int64_t n_out,
+                                                        float *dst, int64_t dst_stride) {
+    const int64_t row = blockIdx.y;
+    const int64_t j0 = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
+    if (j0 >= n_out) return;
+    const typename Elem<DT>::T *sp = src + row * src_stride + 2 * j0;
+    const float sc = scale ? scale[row] : 1.f;
+    const float of = (scale && offset) ? offset[row] : 0.f;
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (j0 + q < n_out) {
+            float a = Elem<DT>::cvt(sp[2 * q]), b = Elem<DT>::cvt(sp[2 * q + 1]);
+            if (scale) { a = fmaf(sc, a, of); b = fmaf(sc, b, of); }
+            o[q] = __fadd_rn(a, b);
+        }
+    }
+    float *dp = dst + row * dst_stride + j0;
+    if (j0 + 4 <= n_out && (reinterpret_cast<uintptr_t>(dp) & 15) == 0) {
+        *reinterpret_cast<float4 *>(dp) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+        for (int q = 0; q < 4 && j0 + q < n_out; ++q) dp[q] = o[q];
+    }
+}
+
+cudaError_t launch_decimate2(const spd_plane &p, float *dst, int64_t n_out, int64_t dst_stride,
+                             cudaStream_t s) {
+    if (p.n_dm <= 0 || n_out <= 0) return cudaSuccess;
+    for (int64_t r0 = 0; r0 < p.n_dm; r0 += 65535) {   // grid.y limit
+        const int64_t y = p.n_dm - r0 < 65535 ? p.n_dm - r0 : 65535;
+        const dim3 grid((unsigned)((n_out + 1023) / 1024), (unsigned)y);
+        const float *sc = p.row_scale ? p.row_scale + r0 : nullptr;
+        const float *of = p.row_offset ? p.row_offset + r0 : nullptr;
+        float *d = dst + r0 * dst_stride;
+        switch (p.dtype) {
+            case SPD_F32:
+                decimate2_kernel<SPD_F32><<<grid, 256, 0, s>>>(
+                    static_cast<const float *>(p.data) + r0 * p.row_stride, p.row_stride, sc, of,
+                    n_out, d, dst_stride);
+                break;
+            case SPD_F16:
+                decimate2_kernel<SPD_F16><<<grid, 256, 0, s>>>(
+                    static_cast<const __half *>(p.data) + r0 * p.row_stride, p.row_stride, sc, of,
+                    n_out, d, dst_stride);
+                break;
+            default:
+                decimate2_kernel<SPD_BF16><<<grid, 256, 0, s>>>(
+                    static_cast<const __nv_bfloat16 *>(p.data) + r0 * p.row_stride, p.row_stride,
+                    sc, of, n_out, d, dst_stride);
+                break;
+        }
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,
                              int64_t n_samp, int64_t stride, float thr, spd_candidate *out,
                              int64_t capacity, spd_result *result, cudaStream_t s) {

@@ -306,7 +306,9 @@ __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
         else if (a.sigma_mode == SPD_SIGMA_LINEAR_EXCESS)
             sw += (w - 1.0) * (m.sd_nmax - sqrt(nm) * m.sd) / (nm - 1.0);
         const bool bad = !(sw > 0.0) || !isfinite(sw);
-        a.inv_tab[(int64_t)e * prog.n_eval + k] = bad ? 0.f : (float)(1.0 / sw);
+        // a NaN 1/sigma makes every SNR of that width NaN, which no max keeps
+        a.inv_tab[(int64_t)e * prog.n_eval + k] =
+            (a.skip_w1 && k == 0) ? __int_as_float(0x7fc00000) : bad ? 0.f : (float)(1.0 / sw);
         if (bad) deg = true;
     }
     deg = __syncthreads_or(deg);

@@ -56,7 +56,8 @@ def test_ctypes_layouts_match_the_c_compiler(tmp_path):
     structs = {"spd_plane": b.SpdPlane, "spd_msd_stats": b.SpdMsdStats,
                "spd_candidate": b.SpdCandidate, "spd_result": b.SpdResult,
                "spd_search_params": b.SpdSearchParams, "spd_range": b.SpdRange,
-               "spd_tuning": b.SpdTuning, "spd_stream_info": b.SpdStreamInfo}
+               "spd_tuning": b.SpdTuning, "spd_stream_info": b.SpdStreamInfo,
+               "spd_msd_part": b.SpdMsdPart, "spd_level": b.SpdLevel}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spd.h"',
              "int main(void) {"]
     for cname, ct in structs.items():
@@ -97,6 +98,31 @@ def test_stream_host_validation(lib):
                                 ctypes.byref(prm), None) == SPD_ERR_INVALID_ARG
     assert lib.spd_stream_reset(ctypes.byref(info), None, 16, 0, ctypes.byref(prm),
                                 None) == SPD_ERR_INVALID_ARG
+
+
+def test_decimated_host_validation(lib):
+    from paper_1611_09704_gb300.binding import SpdLevel
+    p = _plane(4, 1000)
+
+    def levels(*lv):
+        arr = (SpdLevel * len(lv))()
+        keep = []
+        for i, (l, w) in enumerate(lv):
+            a = np.ascontiguousarray(w, dtype=np.int32)
+            keep.append(a)
+            arr[i] = SpdLevel(l, a.size, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        return arr, keep
+
+    ok, k1 = levels((0, [1, 2, 4]), (1, [3, 4]), (3, [2, 4]))
+    assert lib.spd_search_decimated_workspace_bytes(ctypes.byref(p), ok, 3) > 4 * 500 * 4
+    # native widths must ascend across levels (level 1 width 2 = native 4 <= 4)
+    bad, k2 = levels((0, [1, 2, 4]), (1, [2, 4]))
+    assert lib.spd_search_decimated_workspace_bytes(ctypes.byref(p), bad, 2) == 0
+    # levels must ascend and stay within range
+    bad, k3 = levels((1, [2]), (1, [4]))
+    assert lib.spd_search_decimated_workspace_bytes(ctypes.byref(p), bad, 2) == 0
+    bad, k4 = levels((13, [2]),)
+    assert lib.spd_search_decimated_workspace_bytes(ctypes.byref(p), bad, 1) == 0
 
 
 def _plane(n_dm=4, n_samp=100, stride=None, data=4096, dtype=0):

@@ -289,6 +289,29 @@ def test_algorithm1_against_brute_force(seed):
         assert np.array_equal(win[r], ww)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_listed_widths_only_against_brute_force(seed):
+    """start_w1=False (decimated levels): the winner among the listed widths
+    alone, -inf / width 0 where no listed width fits."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(1, 40))
+    x = rng.integers(-3, 4, size=(1, n)).astype(np.float32)
+    widths = np.sort(rng.choice(np.arange(2, 9), size=int(rng.integers(1, 6)), replace=False))
+    mu, sd = -0.5, 2.0
+    tab = oracle.sigma_table(oracle.SIGMA_SQRTN, sd, widths)
+    best, win = oracle.boxcar_snr(x, [mu], [sd], tab, widths, start_w1=False)
+    c = np.concatenate([[0.0], np.cumsum(x[0].astype(np.float64))])
+    for i in range(n):
+        fits = [w for w in widths if i + w <= n]
+        if not fits:
+            assert best[0, i] == -np.inf and win[0, i] == 0
+            continue
+        snr = [(c[i + w] - c[i] - w * mu) / (math.sqrt(w) * sd) for w in fits]
+        k = int(np.argmax(snr))
+        assert best[0, i] == pytest.approx(snr[k], rel=1e-13, abs=1e-13)
+        assert win[0, i] == fits[k]
+
+
 def test_tie_rule_smallest_width_wins():
     """x = (1, 0, 0, ...) with sigma_w = 1 for all w: every width has SNR 1 at
     sample 0, and strict '>' keeps width 1."""
@@ -423,3 +446,77 @@ def test_stream_replay_single_chunk_is_one_shot():
     allc = np.concatenate(rep)
     allc.sort(order=["dm", "sample"])
     assert np.array_equal(one, allc)
+
+
+def test_threshold_plane_cases_and_list_agreement():
+    """Sec. 2.4 on the plane: kept iff >= f_T (exactly f_T kept, the float
+    below it and NaN zeroed); the kept entries are the candidate list."""
+    thr = 6.5
+    best = np.array([[thr, np.nextafter(thr, -np.inf), np.nan, 9.0, -7.0, 0.0]])
+    width = np.array([[3, 4, 5, 6, 7, 8]], np.int32)
+    b, w = oracle.threshold_plane(best, width, thr)
+    assert b.tolist() == [[thr, 0.0, 0.0, 9.0, 0.0, 0.0]]
+    assert w.tolist() == [[3, 0, 0, 6, 0, 0]]
+    rng = np.random.default_rng(4)
+    best = rng.normal(0, 3, (7, 300))
+    width = rng.integers(1, 64, best.shape).astype(np.int32)
+    b, w = oracle.threshold_plane(best, width, 4.0)
+    c = oracle.threshold(best, width, 4.0)
+    nz = np.argwhere(b != 0)
+    assert [tuple(x) for x in nz] == list(zip(c["dm"], c["sample"]))
+    assert np.array_equal(b[b != 0], c["snr"]) and np.array_equal(w[b != 0], c["width"])
+
+
+# ------------------------------------------------------- decimation in time
+
+def test_decimate_ramp_closed_form():
+    n, a, b = 40, 3.0, 0.5
+    x = (a + b * np.arange(n)).astype(np.float32).reshape(1, -1)
+    for level in range(4):
+        m = 1 << level
+        j = np.arange(n >> level)
+        want = m * a + b * (m * m * j + m * (m - 1) / 2)
+        assert np.array_equal(oracle.decimate(x, level)[0], want)
+
+
+def test_decimated_boxcar_is_the_plain_boxcar_at_aligned_starts():
+    """B^l_w(j) on the decimated series = B_{w 2^l}(j 2^l) on the native one
+    (integer data: every sum exact)."""
+    rng = np.random.default_rng(8)
+    x = rng.integers(-50, 50, (3, 203)).astype(np.float32)
+    for level in (1, 2, 3):
+        xl = oracle.decimate(x, level).astype(np.float32)
+        for w in (1, 3, 5):
+            bl = oracle.boxcar_sums(xl, w)
+            bn = oracle.boxcar_sums(x, w << level)
+            n = xl.shape[1] - w + 1
+            assert np.array_equal(bl[:, :n], bn[:, :(n << level):(1 << level)])
+
+
+def test_search_decimated_level0_is_the_plain_search():
+    import synth
+    sp = synth.plain_tophat(6, 5000, device="cpu", seed=12)
+    x = synth.to_host_numpy(sp.data)
+    widths = list(range(1, 33))
+    one, *_ = oracle.search(x, widths, 6.0)
+    got, msds = oracle.search_decimated(x, [(0, widths)], 6.0)
+    assert np.array_equal(got["dm"], one["dm"]) and np.array_equal(got["sample"], one["sample"])
+    assert np.array_equal(got["width"], one["width"]) and np.array_equal(got["snr"], one["snr"])
+
+
+def test_search_decimated_noise_scaling_and_aligned_tophat():
+    """On N(0,1) noise the level-l sd is sqrt(2^l) (3 standard errors); a
+    top-hat of 2^l w samples starting at a multiple of 2^l is found at level l
+    with width 2^l w and an SNR near its plain matched SNR."""
+    rng = np.random.default_rng(9)
+    x = rng.normal(0, 1, (4, 1 << 16)).astype(np.float32)
+    level, w = 3, 8               # native width 64
+    t0, snr = 8 * 1000, 25.0
+    x[2, t0:t0 + (w << level)] += snr / np.sqrt(w << level)
+    got, msds = oracle.search_decimated(x, [(0, list(range(1, 17))), (level, [4, 8, 16])], 7.0)
+    n_l = x.size >> level
+    assert abs(msds[1][1] / np.sqrt(1 << level) - 1) < 3 / np.sqrt(2 * n_l)
+    hit = got[(got["dm"] == 2) & (got["level"] == level)]
+    top = hit[np.argmax(hit["snr"])]
+    assert top["sample"] == t0 and top["width"] == w << level
+    assert abs(top["snr"] - snr) < 4.0
