@@ -37,6 +37,7 @@ SAMPLE_TIME_S = 64e-6
 # msd_partial, msd_merge_l1, fold_final, merge_shards, consts, detect
 KERNELS_PER_STEP = 6
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "detect_traffic.txt")
+E2E_DEPTH = 3          # planes in flight in the end-to-end measurement
 DETECT_SRC = os.path.join(ROOT, "paper_1611_09704_gb300", "csrc", "spd_detect_kernel.cuh")
 
 
@@ -48,7 +49,7 @@ def parse():
     ap.add_argument("--impl", choices=["spd", "reference"], default="spd")
     ap.add_argument("--n-dm", type=int, default=4096)
     ap.add_argument("--n-samp", type=int, default=524288)
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=512)
@@ -333,8 +334,10 @@ def e2e(x, count, steps, n, world, rank, dev):
     xh.copy_(x)
     n_dm, n_samp = x.shape
     cap = int(n * 0.45) + 1024
-    pp = PlanePipeline(n_dm, n_samp, WIDTHS, THRESHOLD, cap, dtype=x.dtype, depth=2, device=dev,
-                       dm_offset=rank * n_dm, host_capacity=count + (count >> 4) + 1024)
+    depth = E2E_DEPTH
+    pp = PlanePipeline(n_dm, n_samp, WIDTHS, THRESHOLD, cap, dtype=x.dtype, depth=depth,
+                       device=dev, dm_offset=rank * n_dm,
+                       host_capacity=count + (count >> 4) + 1024)
     # one untimed plane (lazy set-up, page-in of the host buffers)
     r = pp.collect(pp.submit(xh))
     if r[0] != count:
@@ -344,13 +347,13 @@ def e2e(x, count, steps, n, world, rank, dev):
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tickets = [pp.submit(xh) for _ in range(min(2, steps))]
+    tickets = [pp.submit(xh) for _ in range(min(depth, steps))]
     for k in range(steps):
         c, st, recs = pp.collect(tickets[k])
         if st != 0:
             raise RuntimeError(f"pipeline status {st}")
         d2h.append(16 + 16 * recs.shape[0])
-        if k + 2 < steps:
+        if k + depth < steps:
             tickets.append(pp.submit(xh))
     t = (time.perf_counter() - t0) / steps
     if world > 1:
@@ -362,8 +365,8 @@ def e2e(x, count, steps, n, world, rank, dev):
     return {"value": world * n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
             "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3,
             "steps": steps,
-            "api": "PlanePipeline (sharded search over the C ABI) from page-locked host "
-                   "memory, 2 planes in flight"}
+            "api": f"PlanePipeline (sharded search over the C ABI) from page-locked host "
+                   f"memory, {depth} planes in flight"}
 
 
 def timed(step, steps, warmup, clocks_dev):
