@@ -49,7 +49,9 @@ namespace {
 
 constexpr int kPad = 20;             // shared words per 16 positions
 constexpr int kMaxLevel = 5;         // sparse max table: windows up to 2^5 blocks
-constexpr int kWaitLimit = 1 << 22;  // bounded spin on a bulk copy (seconds)
+constexpr uint64_t kWaitNs = 2000000000ull;  // a bulk copy not done in 2 s is reported
+constexpr int kWaitLimit = 1 << 24;          // polls, a backstop to the time bound
+constexpr uint32_t kSuspendNs = 20000;       // suspend hint of one poll
 
 __device__ __forceinline__ int padr(int p) { return (p & 15) + kPad * (p >> 4); }
 
@@ -96,20 +98,32 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         ::"r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar))
         : "memory");
 }
+// One poll; the thread may be suspended (up to kSuspendNs) until the phase
+// completes instead of spinning on issue slots.
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(saddr(bar)), "r"(phase)
+        : "r"(saddr(bar)), "r"(phase), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for a phase of `bar`; false if it did not complete in time.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for a phase of `bar`: false if it did not complete within
+// kWaitNs of wall time (or kWaitLimit polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
-    for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_test(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < kWaitLimit; ++it) {
         if (mbar_test(bar, phase)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 
@@ -543,15 +557,16 @@ __device__ void build_stats(const float *s_y, float *s_g, float *s_bs, float *s_
 // with the group's largest 1/sigma_w.  *s_kmax = the highest level any group
 // reads.
 __device__ __forceinline__ void load_range_consts(const RangeDesc &rd, int entry, float *s_inv,
-                                                  uint16_t *s_ew, int4 *s_gb, int *s_kmax,
-                                                  bool bounds) {
+                                                  uint16_t *s_ew, int4 *s_gb, Group *s_grp,
+                                                  int *s_kmax, bool bounds) {
     const RangeProg &rp = rd.prog;
+    for (int gi = threadIdx.x; gi < rp.n_groups; gi += kThreads) s_grp[gi] = rp.groups[gi];
     for (int q = threadIdx.x; q < rp.n_eval; q += kThreads)
         s_inv[q] = rd.inv_tab[(int64_t)entry * rp.n_eval + q];
     if (threadIdx.x == 0) *s_kmax = 0;
     __syncthreads();
     for (int gi = threadIdx.x; gi < rp.n_groups; gi += kThreads) {
-        const Group g = rp.groups[gi];
+        const Group g = s_grp[gi];
         const int d = (g.flags & kGroupCoarse) ? rp.G : 1;
         float mxv = 0.f;
         for (int c = 0; c < g.count; ++c) {
@@ -581,23 +596,26 @@ __device__ __forceinline__ void build_max_table(const float *s_mx, float *s_st, 
     __syncthreads();
     const int k3 = kmax < 3 ? kmax : 3;
     for (int c = threadIdx.x; c < R; c += kThreads) {
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            v[j] = (j < (1 << k3) && c + j < R) ? s_mx[c + j] : -INFINITY;
-        const float m1 = fmaxf(v[0], v[1]);
-        const float m2 = fmaxf(m1, fmaxf(v[2], v[3]));
-        const float m3 = fmaxf(m2, fmaxf(fmaxf(v[4], v[5]), fmaxf(v[6], v[7])));
+        // blocks past the end repeat the last one (max is unchanged by it)
+        const float m1 = fmaxf(s_mx[c], s_mx[min(c + 1, R - 1)]);
         s_st[c] = m1;
-        if (k3 >= 2) s_st[RM + c] = m2;
-        if (k3 >= 3) s_st[2 * RM + c] = m3;
+        if (k3 >= 2) {
+            const float m2 = fmaxf(m1, fmaxf(s_mx[min(c + 2, R - 1)], s_mx[min(c + 3, R - 1)]));
+            s_st[RM + c] = m2;
+            if (k3 >= 3) {
+                float m3 = m2;
+#pragma unroll
+                for (int j = 4; j < 8; ++j) m3 = fmaxf(m3, s_mx[min(c + j, R - 1)]);
+                s_st[2 * RM + c] = m3;
+            }
+        }
     }
     for (int k = 4; k <= kmax; ++k) {
         __syncthreads();
         const float *lo = s_st + (k - 2) * RM;
         const int h = 1 << (k - 1);
         for (int c = threadIdx.x; c < R; c += kThreads)
-            s_st[(k - 1) * RM + c] = fmaxf(lo[c], c + h < R ? lo[c + h] : -INFINITY);
+            s_st[(k - 1) * RM + c] = fmaxf(lo[c], lo[min(c + h, R - 1)]);
     }
     __syncthreads();
 }
@@ -620,6 +638,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         (reinterpret_cast<uintptr_t>(s_inv + L.max_eval) + 15) & ~(uintptr_t)15);
     uint16_t *s_ew = reinterpret_cast<uint16_t *>(s_gb + kMaxCodeGroups);
     __shared__ int s_kmax;
+    __shared__ Group s_grp[kMaxCodeGroups];   // the range's width groups
     __shared__ int s_wsum[kThreads / 32];
     __shared__ unsigned long long s_base;
     __shared__ float s_wt[3 * (kThreads / 32) + 3 * kThreads];
@@ -662,17 +681,32 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
     if (tma && tid == 0 && (int64_t)blockIdx.x < n_tiles)
         issue(blockIdx.x, range_of(blockIdx.x, 0), 0);
 
-    int k = 0, ri = 0;
+    int k = 0, ri = 0, cur_ri = -1;
     int64_t key = -1;   // (range, scope entry) whose constants are in shared memory
+    int64_t row = 0, col = 0;   // the tile's row and tile column within its range
+    int64_t step_rows = 0, step_cols = 0;   // gridDim.x tiles as rows + columns of the range
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
         const int buf = k & 1;
         ri = range_of(tile, ri);
         const RangeDesc &rd = L.rng[ri];
         const RangeProg &rp = rd.prog;
         const int R = rd.R;
-        const int64_t lt = tile - rd.tile0;
-        const int64_t row = lt / rd.tiles_per_row;
-        const int64_t t0 = (lt - row * rd.tiles_per_row) * (int64_t)kTile;
+        if (ri != cur_ri) {   // first tile of a range: divisions once
+            const int64_t lt = tile - rd.tile0;
+            row = lt / rd.tiles_per_row;
+            col = lt - row * rd.tiles_per_row;
+            step_rows = (int64_t)gridDim.x / rd.tiles_per_row;
+            step_cols = (int64_t)gridDim.x - step_rows * rd.tiles_per_row;
+            cur_ri = ri;
+        } else {              // the next tile of this CTA: gridDim.x tiles on
+            row += step_rows;
+            col += step_cols;
+            if (col >= rd.tiles_per_row) {
+                col -= rd.tiles_per_row;
+                ++row;
+            }
+        }
+        const int64_t t0 = col * (int64_t)kTile;
         const int entry = rd.per_row ? (int)row : 0;
         const int64_t i0 = t0 + (int64_t)tid * kX;   // first start sample of this thread
         const T *rowp = static_cast<const T *>(rd.data) + row * rd.stride;
@@ -697,22 +731,30 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         const bool has_sc = rd.scale != nullptr;
         const float sc = has_sc ? rd.scale[row] : 1.f;
         const float of = (has_sc && rd.offset) ? rd.offset[row] : 0.f;
-        const int64_t have = min((int64_t)rd.span, rd.n_samp - t0);
-        const int nraw = tma ? (int)(((have * esz) & ~(int64_t)15) / esz) : 0;
+        const int have = (int)min((int64_t)rd.span, rd.n_samp - t0);   // window samples in the row
+        const int nraw = tma ? (int)((((int64_t)have * esz) & ~(int64_t)15) / esz) : 0;
         const T *raw = reinterpret_cast<const T *>(s_raw0 + buf * L.raw_bytes);
 
         if (!deg) {
             const int64_t nk = ((int64_t)ri << 32) | (uint32_t)entry;
             if (nk != key) {
-                load_range_consts(rd, entry, s_inv, s_ew, s_gb, &s_kmax, !PLANE);
+                load_range_consts(rd, entry, s_inv, s_ew, s_gb, s_grp, &s_kmax, !PLANE);
                 key = nk;
             }
             // Stage centred samples; -inf past the row end and past the window.
             for (int q = tid; q < 4 * R; q += kThreads) {
                 const int p = 4 * q;
                 float x[4];
-                if (p + 3 < nraw) {
+                if (p + 3 < nraw) {   // the common case: four copied samples
                     load4v<DT>(raw + p, x[0], x[1], x[2], x[3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (has_sc) x[e] = fmaf(sc, x[e], of);
+                        x[e] = __fsub_rn(__fsub_rn(x[e], mu.x), mu.y);
+                    }
+                    *reinterpret_cast<float4 *>(s_y + padr(p)) =
+                        make_float4(x[0], x[1], x[2], x[3]);
+                    continue;
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
@@ -770,7 +812,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
             for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
             int cur = 0;   // block of 64 eval indices being packed
             for (int gi = 0; gi < rp.n_groups; ++gi) {
-                const Group g = rp.groups[gi];
+                const Group g = s_grp[gi];
                 if (MG && (g.widx0 >> 6) != cur) {
                     // blocks of 64 widths: a later block wins only with a larger
                     // value (its code bits say nothing about earlier blocks)
@@ -860,7 +902,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
             const float bound = ub > 0.f ? (ub + slack) * __int_as_float(gb.w) * 1.00001f : 0.f;
             // a NaN bound (window past the row end) falls through to evaluation
             if (bound + 1e-5f * fabsf(lim) < lim) continue;
-            const Group g = rp.groups[gi];
+            const Group g = s_grp[gi];
             mk.reset();
             group_start(B, s_y, s_bs, tid, g.off);
             run_group<G>(B, mk, sy_t, sg_t, g, s_inv);
@@ -876,15 +918,21 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         uint32_t mask = 0;
         uint64_t need = 0;
         uint32_t wcode[kX / 4];   // winning group code of sample q: byte q & 3 of wcode[q >> 2]
+        {
+            const int64_t ne = rd.n_emit - i0;   // starts of this unit that may be emitted
+            const int lim = ne <= 0 ? 0 : (ne >= kX ? kX : (int)ne);
+#pragma unroll
+            for (int q = 0; q < kX; ++q)
+                if (q < lim && trunc17(best[q]) >= thr) mask |= 1u << q;
+        }
 #pragma unroll
         for (int q = 0; q < kX / 4; ++q) wcode[q] = 0;
+        if (mask) {
 #pragma unroll
-        for (int q = 0; q < kX; ++q) {
-            const uint32_t code = __float_as_uint(best[q]) & 63u;
-            wcode[q >> 2] |= code << (8 * (q & 3));
-            if (i0 + q < rd.n_emit && trunc17(best[q]) >= thr) {
-                mask |= 1u << q;
-                need |= 1ull << (63u - code);
+            for (int q = 0; q < kX; ++q) {
+                const uint32_t code = __float_as_uint(best[q]) & 63u;
+                wcode[q >> 2] |= code << (8 * (q & 3));
+                if ((mask >> q) & 1u) need |= 1ull << (63u - code);
             }
         }
         // block-aggregated compaction: one atomic per CTA reserves the tile's
@@ -929,7 +977,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         while (need) {
             const int gi = __ffsll((long long)need) - 1;
             need &= need - 1;
-            const Group g = rp.groups[gi];
+            const Group g = s_grp[gi];
             PackSink rk;
 #pragma unroll
             for (int q = 0; q < kX; ++q) rk.best[q] = -INFINITY;
