@@ -90,7 +90,7 @@ MsdLayout msd_layout(const spd_plane *p, int nmax = 0) {
 // by the listed widths.  They are cut into groups of consecutive widths that
 // step by 1 (the running sum adds one sample per width) or by G (it adds one
 // G-sample window sum); a group's sums start from the block sums at `off`.
-// Groups hold at most 16 (step 1) or 2 (16/G + 1) (step G) widths times
+// Groups hold at most 16 (step 1) or 4 (16/G + 1) (step G) widths times
 // `scale`, doubled until there are at most 64 groups, and never cross a
 // multiple of 64 in eval index.  G is the most frequent step of 8 or 16, if any.
 spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, int scale0 = 1) {
@@ -113,7 +113,9 @@ spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, in
 
     std::vector<Group> groups;
     for (int scale = scale0 < 1 ? 1 : scale0;; scale *= 2) {
-        const int max_fine = 16 * scale, max_coarse = (G ? 2 * (16 / G + 1) : 1) * scale;
+        // coarse groups hold 4 (16 / G + 1) widths at scale 1: their start and
+        // merge cost more than a fine group's relative to their widths
+        const int max_fine = 16 * scale, max_coarse = (G ? 4 * (16 / G + 1) : 1) * scale;
         groups.clear();
         for (int k = 0; k < ne; ++k) {
             const int step = k ? E[k] - E[k - 1] : 1;
