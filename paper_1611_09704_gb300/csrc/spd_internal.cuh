@@ -62,7 +62,7 @@ struct NmaxArgs {
     int vec_ok;                 // rows aligned for 4-element vector loads
     int nmax;
     int nb;                     // staged blocks of 16 samples per tile
-    int64_t tiles_per_row;
+    int64_t tiles_per_row;      // partials per row (each covers up to 8 tiles of 4096 starts)
     MsdPart *parts;             // [n_dm * tiles_per_row]
 };
 
@@ -166,6 +166,7 @@ cudaError_t launch_stream_msd(const MsdPart *parts, int64_t n_dm, int64_t upr, i
                               MsdPart *state, spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_zero_parts(MsdPart *p, int64_t n, cudaStream_t s);
 int nmax_blocks(int nmax);
+// sigma_Nmax partials per row (CTAs of the partial kernel per row).
 int64_t nmax_tiles_per_row(int64_t n_samp);
 cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s);
 // Fold n_parts partials into *out (the block tree of the final merge).

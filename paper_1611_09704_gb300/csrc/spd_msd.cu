@@ -323,16 +323,18 @@ __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
 
 // ----------------------------------------------------- sigma_Nmax (Eq. 5)
 
-constexpr int kNmaxTile = 4096;        // start samples per CTA
+constexpr int kNmaxTile = 4096;        // start samples of one tile
 constexpr int kNmaxPer = kNmaxTile / kMsdThreads;   // 16 consecutive starts per thread
+constexpr int kNmaxTilesPerCta = 8;    // consecutive tiles of one row per CTA (one partial)
 
 // Sec. 2.2, Eq. 5 needs sigma_Nmax, the measured sd of the boxcar series
-// B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA stages the
-// centred samples of one tile plus an (Nmax - 1)-sample halo, forms B for its
-// 16 consecutive starts per thread (whole-block sums plus partial sums for the
-// first start, then sliding one sample), and reduces them to (n, T, S) with
-// Eq. 1 per thread and Eq. 2 across lanes and warps.  The sd does not depend
-// on the centring.
+// B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA walks up
+// to kNmaxTilesPerCta consecutive tiles of one row; per tile it stages the
+// centred samples plus an (Nmax - 1)-sample halo and forms B for its 16
+// consecutive starts per thread (whole-block sums plus partial sums for the
+// first start, then sliding one sample), adding them with Eq. 1 to the
+// thread's running (n, T, S).  At the end Eq. 2 merges across lanes and warps
+// into the CTA's one partial.  The sd does not depend on the centring.
 template <int DT>
 __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArgs a) {
     using T = typename Elem<DT>::T;
@@ -341,8 +343,11 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArg
     extern __shared__ __align__(16) float s_y[];   // [nb * 20]
     float *s_bs = s_y + 20 * a.nb;                 // [nb] block sums
     const int tid = threadIdx.x;
-    const int64_t row = blockIdx.x / a.tiles_per_row;
-    const int64_t t0 = (blockIdx.x - row * a.tiles_per_row) * (int64_t)kNmaxTile;
+    const int64_t row = blockIdx.x / a.tiles_per_row;   // tiles_per_row: partials per row
+    const int64_t part = blockIdx.x - row * a.tiles_per_row;
+    const int64_t tiles_in_row = (a.n_samp + kNmaxTile - 1) / kNmaxTile;
+    const int64_t tl0 = part * kNmaxTilesPerCta;
+    const int64_t tl1 = min(tl0 + kNmaxTilesPerCta, tiles_in_row);
     const int entry = a.per_row ? (int)row : 0;
     const double mu = a.msd[entry].mean;
     const float mh = (float)mu, ml = (float)(mu - (double)mh);
@@ -350,88 +355,92 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArg
     const bool has_sc = a.scale != nullptr;
     const float sc = has_sc ? a.scale[row] : 1.f;
     const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
-    for (int q4 = tid; q4 < 4 * a.nb; q4 += kMsdThreads) {
-        const int p = 4 * q4;
-        float x[4];
-        if (a.vec_ok && t0 + p + 3 < a.n_samp) {
-            load4<DT>(rp + t0 + p, x[0], x[1], x[2], x[3]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                x[e] = t0 + p + e < a.n_samp ? Elem<DT>::cvt(rp[t0 + p + e]) : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (has_sc) x[e] = fmaf(sc, x[e], of);
-            x[e] = t0 + p + e < a.n_samp ? (x[e] - mh) - ml : 0.f;
-        }
-        *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
-            make_float4(x[0], x[1], x[2], x[3]);
-    }
-    __syncthreads();
-    for (int b = tid; b < a.nb; b += kMsdThreads) {
-        float sum = 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * b + 4 * q);
-            sum += (f.x + f.y) + (f.z + f.w);
-        }
-        s_bs[b] = sum;
-    }
-    __syncthreads();
-
     const int nmax = a.nmax;
     const int p0 = tid * kNmaxPer;                 // first start of this thread (tile-local)
     const int qe = p0 + nmax;
-    // B at p0: whole blocks from p0 to p0 + nmax (Kahan), plus the partial
-    // block at the end (p0 is a multiple of 16)
-    float whole = 0.f, comp = 0.f;
-    for (int b = p0 >> 4; b < (qe >> 4); ++b) {
-        const float y = s_bs[b] - comp;
-        const float t = whole + y;
-        comp = (t - whole) - y;
-        whole = t;
-    }
-    float tail = 0.f;
-    for (int q = (qe & ~15); q < qe; ++q) tail += s_y[(q & 15) + 20 * (q >> 4)];
-    float B = whole + tail;
-    // the thread's 16 samples and the 16 that enter the window as it slides
-    float lo[16], hi[16];
+    Acc acc;
+    for (int64_t tl = tl0; tl < tl1; ++tl) {
+        const int64_t t0 = tl * (int64_t)kNmaxTile;
+        __syncthreads();   // the previous tile's reads of s_y / s_bs are done
+        for (int q4 = tid; q4 < 4 * a.nb; q4 += kMsdThreads) {
+            const int p = 4 * q4;
+            float x[4];
+            if (a.vec_ok && t0 + p + 3 < a.n_samp) {
+                load4<DT>(rp + t0 + p, x[0], x[1], x[2], x[3]);
+            } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * tid + 4 * q);
-        lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
-    }
-    if ((nmax & 15) == 0) {
+                for (int e = 0; e < 4; ++e)
+                    x[e] = t0 + p + e < a.n_samp ? Elem<DT>::cvt(rp[t0 + p + e]) : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (has_sc) x[e] = fmaf(sc, x[e], of);
+                x[e] = t0 + p + e < a.n_samp ? (x[e] - mh) - ml : 0.f;
+            }
+            *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+                make_float4(x[0], x[1], x[2], x[3]);
+        }
+        __syncthreads();
+        for (int b = tid; b < a.nb; b += kMsdThreads) {
+            float sum = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * b + 4 * q);
+                sum += (f.x + f.y) + (f.z + f.w);
+            }
+            s_bs[b] = sum;
+        }
+        __syncthreads();
+
+        // B at p0: whole blocks from p0 to p0 + nmax (Kahan), plus the partial
+        // block at the end (p0 is a multiple of 16)
+        float whole = 0.f, comp = 0.f;
+        for (int b = p0 >> 4; b < (qe >> 4); ++b) {
+            const float y = s_bs[b] - comp;
+            const float t = whole + y;
+            comp = (t - whole) - y;
+            whole = t;
+        }
+        float tail = 0.f;
+        for (int q = (qe & ~15); q < qe; ++q) tail += s_y[(q & 15) + 20 * (q >> 4)];
+        float B = whole + tail;
+        // the thread's 16 samples and the 16 that enter the window as it slides
+        float lo[16], hi[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float4 f =
-                *reinterpret_cast<const float4 *>(s_y + 20 * (tid + (nmax >> 4)) + 4 * q);
-            hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
+            const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * tid + 4 * q);
+            lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
         }
-    } else {
+        if ((nmax & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f =
+                    *reinterpret_cast<const float4 *>(s_y + 20 * (tid + (nmax >> 4)) + 4 * q);
+                hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int q = p0 + k + nmax;
+                hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+            }
+        }
+        float bw[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int q = p0 + k + nmax;
-            hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+            bw[k] = B;
+            B = (B - lo[k]) + hi[k];
         }
-    }
-    float bw[16];
+        // starts t0 + p0 + k are full windows while t0 + p0 + k + nmax <= n_samp
+        const int64_t nvalid = a.n_samp - nmax - (t0 + p0) + 1;
+        if (nvalid >= 16) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        bw[k] = B;
-        B = (B - lo[k]) + hi[k];
-    }
-    // starts t0 + p0 + k are full windows while t0 + p0 + k + nmax <= n_samp
-    const int64_t nvalid = a.n_samp - nmax - (t0 + p0) + 1;
-    Acc acc;
-    if (nvalid >= 16) {
+            for (int k = 0; k < 16; k += 4) acc.add4(bw[k], bw[k + 1], bw[k + 2], bw[k + 3]);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 16; k += 4) acc.add4(bw[k], bw[k + 1], bw[k + 2], bw[k + 3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < nvalid) acc.add1(bw[k]);
+            for (int k = 0; k < 16; ++k)
+                if (k < nvalid) acc.add1(bw[k]);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc.merge_down(off);
@@ -574,7 +583,10 @@ cudaError_t launch_msd_merge(const MsdPart *parts, int64_t n_dm, int64_t upr, in
 }
 
 int nmax_blocks(int nmax) { return (kNmaxTile + nmax + 15) / 16 + 1; }
-int64_t nmax_tiles_per_row(int64_t n_samp) { return (n_samp + kNmaxTile - 1) / kNmaxTile; }
+int64_t nmax_tiles_per_row(int64_t n_samp) {
+    const int64_t tiles = (n_samp + kNmaxTile - 1) / kNmaxTile;
+    return (tiles + kNmaxTilesPerCta - 1) / kNmaxTilesPerCta;   // partials per row
+}
 
 cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
