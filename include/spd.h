@@ -420,6 +420,16 @@ spd_status spd_search_decimated(const spd_plane *plane, const spd_level *levels,
                                 spd_result *result_dev, spd_msd_stats *msd_out_dev,
                                 void *workspace, size_t workspace_bytes, void *stream);
 
+/* Test aid, for the calling host thread's later searches: every wait of the
+ * fused kernel for a bulk copy of a tile gives up after limit_ns (1 ms ..
+ * 10 s; default 2 s), and extra_bytes (a multiple of 16, at most 4096; 0 in
+ * use) more bytes than the copy delivers are expected, so that with
+ * extra_bytes > 0 every wait runs out: the kernel sets SPD_ERR_TIMEOUT in the
+ * result word and its CTAs leave (each copy itself has landed, so nothing is
+ * left in flight).  spd_debug_set_copy_wait(2000000000, 0) restores the
+ * default.  Errors: SPD_ERR_INVALID_ARG. */
+spd_status spd_debug_set_copy_wait(uint64_t limit_ns, uint32_t extra_bytes);
+
 /* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
  * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */
 spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out,

@@ -104,7 +104,8 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_stream_push", "spd_stream_chunk_view", "spd_stream_flush",
            "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
            "spd_sd_nmax_merge_partials", "spd_threshold_plane",
-           "spd_search_decimated_workspace_bytes", "spd_search_decimated"]
+           "spd_search_decimated_workspace_bytes", "spd_search_decimated",
+           "spd_debug_set_copy_wait"]
 
 
 class SpdError(RuntimeError):
@@ -169,6 +170,8 @@ def load(path: str | None = None):
     lib.spd_search_batched_workspace_bytes.restype = SZ
     lib.spd_search_batched.argtypes = [pr, I32, pt, P, I64, P, P, P, SZ, P]
     lib.spd_search_batched.restype = I32
+    lib.spd_debug_set_copy_wait.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+    lib.spd_debug_set_copy_wait.restype = I32
     plv = ctypes.POINTER(SpdLevel)
     lib.spd_search_decimated_workspace_bytes.argtypes = [pp, plv, I32]
     lib.spd_search_decimated_workspace_bytes.restype = SZ
@@ -444,6 +447,14 @@ def search(x, widths, threshold, capacity, sigma_mode=SIGMA_SQRTN, scope=MSD_GLO
            "spd_search")
     del keep
     return out, result, msd_out
+
+
+def debug_set_copy_wait(limit_ns=2_000_000_000, extra_bytes=0):
+    """spd_debug_set_copy_wait (test aid): bound of the fused kernel's waits
+    for tile copies, and bytes expected beyond each copy (> 0 makes every wait
+    run out); the defaults restore normal operation."""
+    _check(load().spd_debug_set_copy_wait(int(limit_ns), int(extra_bytes)),
+           "spd_debug_set_copy_wait")
 
 
 def boxcar_sums(x, w, *, stream=None, out=None, **kw):

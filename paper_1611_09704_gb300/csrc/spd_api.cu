@@ -248,6 +248,11 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
     return SPD_OK;
 }
 
+// Bound of a wait for a bulk copy, and bytes expected beyond each copy (a
+// test aid that makes the waits run out); set by spd_debug_set_copy_wait.
+thread_local uint64_t g_wait_ns = 2000000000ull;
+thread_local uint32_t g_extra_tx = 0;
+
 // One detect launch over ranges rd[0 .. n) (same storage type and G).
 spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out, int64_t cap,
                       spd_result *result, float *snr_out, uint16_t *width_out,
@@ -276,6 +281,8 @@ spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out,
     L.snr_out = snr_out;
     L.width_out = width_out;
     L.out_stride = out_stride;
+    L.wait_ns = g_wait_ns;
+    L.extra_tx = g_extra_tx;
     const size_t smem = launch_smem(R, raw, max_eval, G);
     if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
     SPD_CK(launch_detect(L, dtype, G, snr_out != nullptr, max_eval > 64, smem, ctas_per_sm, st));
@@ -1090,6 +1097,15 @@ spd_status spd_stream_flush(spd_stream_info *info, void *state_dev,
     SPD_TRY(stream_search(info, prog, params, ws + P.comb_off, P.cstride, H, H, scale, offset,
                           stats, out, capacity, result_dev, ws + P.det_off, st));
     info->halo = 0;
+    return SPD_OK;
+}
+
+spd_status spd_debug_set_copy_wait(uint64_t limit_ns, uint32_t extra_bytes) {
+    if (limit_ns < 1000000ull || limit_ns > 10000000000ull || extra_bytes > 4096u ||
+        (extra_bytes & 15u))
+        return SPD_ERR_INVALID_ARG;
+    g_wait_ns = limit_ns;
+    g_extra_tx = extra_bytes;
     return SPD_OK;
 }
 

@@ -49,8 +49,7 @@ namespace {
 
 constexpr int kPad = 20;             // shared words per 16 positions
 constexpr int kMaxLevel = 5;         // sparse max table: windows up to 2^5 blocks
-constexpr uint64_t kWaitNs = 2000000000ull;  // a bulk copy not done in 2 s is reported
-constexpr int kWaitLimit = 1 << 24;          // polls, a backstop to the time bound
+constexpr int kWaitLimit = 1 << 22;          // polls, a backstop to the time bound
 constexpr uint32_t kSuspendNs = 20000;       // suspend hint of one poll
 
 __device__ __forceinline__ int padr(int p) { return (p & 15) + kPad * (p >> 4); }
@@ -116,13 +115,13 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Bounded wait for a phase of `bar`: false if it did not complete within
-// kWaitNs of wall time (or kWaitLimit polls).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+// limit_ns of wall time (or kWaitLimit polls).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, uint64_t limit_ns) {
     if (mbar_test(bar, phase)) return true;
     const uint64_t t0 = global_ns();
     for (int it = 0; it < kWaitLimit; ++it) {
         if (mbar_test(bar, phase)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -672,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         const uint32_t nb = (uint32_t)((have * esz) & ~(int64_t)15);
         uint64_t *bar = s_bar + buf;
         fence_proxy_async();
-        mbar_expect(bar, nb);
+        mbar_expect(bar, nb + L.extra_tx);
         if (nb) {
             const T *src = static_cast<const T *>(rd.data) + row * rd.stride + t0;
             bulk_load(s_raw0 + buf * L.raw_bytes, src, nb, bar);
@@ -716,11 +715,12 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
             // thread's reads after it.  If the copy did not land in time the
             // whole CTA reports it, gives the copy (the only one in flight)
             // one more bounded wait, and leaves.
-            const bool ok = tid != 0 || mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+            const bool ok =
+                tid != 0 || mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1), L.wait_ns);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     if (L.result) atomicExch(&L.result->status, (int)SPD_ERR_TIMEOUT);
-                    mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1));
+                    mbar_wait(s_bar + buf, (uint32_t)((k >> 1) & 1), L.wait_ns);
                 }
                 return;
             }

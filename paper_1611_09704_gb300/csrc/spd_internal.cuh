@@ -142,6 +142,9 @@ struct Launch {
     float *snr_out;             // plane output (single range) or null
     uint16_t *width_out;
     int64_t out_stride;
+    uint64_t wait_ns;           // bound of a wait for a bulk copy
+    uint32_t extra_tx;          // test aid: bytes expected beyond each copy (0 in use)
+    uint32_t reserved0;
     RangeDesc rng[kMaxRanges];
 };
 

@@ -125,6 +125,14 @@ def test_decimated_host_validation(lib):
     assert lib.spd_search_decimated_workspace_bytes(ctypes.byref(p), bad, 1) == 0
 
 
+def test_debug_copy_wait_validation(lib):
+    from paper_1611_09704_gb300.binding import SPD_ERR_INVALID_ARG
+    assert lib.spd_debug_set_copy_wait(100, 0) == SPD_ERR_INVALID_ARG          # under 1 ms
+    assert lib.spd_debug_set_copy_wait(20_000_000, 8) == SPD_ERR_INVALID_ARG   # not 16-byte
+    assert lib.spd_debug_set_copy_wait(20_000_000, 8192) == SPD_ERR_INVALID_ARG
+    assert lib.spd_debug_set_copy_wait(2_000_000_000, 0) == 0
+
+
 def _plane(n_dm=4, n_samp=100, stride=None, data=4096, dtype=0):
     from paper_1611_09704_gb300.binding import SpdPlane
     return SpdPlane(data, dtype, 0, n_dm, n_samp, stride or n_samp, None, None)
