@@ -1,0 +1,124 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+The SKA-like 4096 x 524288 FP32 plane goes through the sharded search path of
+bench.py (one shard), and the four batched ranges through one captured
+batched launch.  The oracle cannot search these planes whole, so it checks:
+- the MSD over the whole plane (FP64 two-pass);
+- sampled outputs, one by one: the SNR and width of candidate records, and
+  the candidate/non-candidate decision at random positions of sampled rows,
+  from direct FP64 boxcar sums (Algorithm 1 at one start)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+SKA_WIDTHS = list(range(1, 17)) + list(range(24, 257, 8))
+CAND = np.dtype([("dm", "<i4"), ("sample", "<i4"), ("snr", "<f4"), ("width", "<i4")])
+
+
+@pytest.fixture(scope="module")
+def spd():
+    import paper_1611_09704_gb300 as m
+    m.build()
+    m.load()
+    return m
+
+
+def _best_at(op, r, i, widths, mean, sd):
+    """Algorithm 1 at one start, from direct sums: (best SNR, its width)."""
+    best, win = oracle.snr_at(op, r, i, 1, mean, sd), 1
+    for w in widths:
+        if w == 1:
+            continue
+        s = oracle.snr_at(op, r, i, w, mean, math.sqrt(w) * sd)
+        if s != s:          # past the row end
+            break
+        if s > best:
+            best, win = s, w
+    return best, win
+
+
+def _check_rows(op, recs_dev, rows, dm_offset, widths, mean, sd, thr, rng, n_cand=120,
+                n_pos=200):
+    """Sampled candidates and sampled positions of the given rows."""
+    n_samp = op.n_samp
+    checked = 0
+    for r in rows:
+        sel = recs_dev[recs_dev[:, 0] == dm_offset + r]
+        recs = sel.cpu().numpy().copy().view(CAND).reshape(-1)
+        samples = set(recs["sample"].tolist())
+        assert len(samples) == len(recs), "duplicate candidates"
+        for k in rng.choice(len(recs), size=min(n_cand, len(recs)), replace=False):
+            rec = recs[k]
+            b, w = _best_at(op, r, int(rec["sample"]), widths, mean, sd)
+            assert b >= thr - P.BAND
+            assert abs(float(rec["snr"]) - b) <= P.SNR_RTOL * max(abs(b), 1.0), (r, rec, b)
+            if int(rec["width"]) != w:   # a tie within the stated tolerance
+                sw = oracle.snr_at(op, r, int(rec["sample"]), int(rec["width"]), mean,
+                                   math.sqrt(int(rec["width"])) * sd)
+                assert sw >= b - P.TIE_RTOL * max(abs(b), 1.0), (r, rec, b, w)
+            checked += 1
+        for i in rng.integers(0, n_samp, size=n_pos):
+            b, _ = _best_at(op, r, int(i), widths, mean, sd)
+            if b >= thr + P.BAND:
+                assert int(i) in samples, (r, i, b)
+            elif b < thr - P.BAND:
+                assert int(i) not in samples, (r, i, b)
+            checked += 1
+    return checked
+
+
+def test_ska_like_full_size_sharded_path(spd):
+    from paper_1611_09704_gb300.sharding import ShardedSearch
+    n_dm, n_samp, thr = 4096, 524288, 7.0
+    x = synth.ska_like(n_dm, n_samp, device=DEV, seed=1611_1).data   # bench.py's plane
+    cap = int(n_dm * n_samp * 0.45) + 1024
+    ss = ShardedSearch(x, SKA_WIDTHS, thr, cap)
+    ss.run()
+    count, status = spd.read_result(ss.result)
+    assert status == 0 and 0 < count <= cap
+    gm = spd.msd_to_numpy(ss.msd)
+    op = oracle.Plane(synth.to_host_numpy(x))
+    mean, sd = oracle.plane_msd(op)
+    P.check_msd(gm, mean, sd)
+    rng = np.random.default_rng(2024)
+    rows = rng.choice(n_dm, size=6, replace=False)
+    n = _check_rows(op, ss.out[:count], rows, 0, SKA_WIDTHS, float(mean[0]), float(sd[0]),
+                    thr, rng)
+    assert n > 1000
+
+
+def test_batched_full_size_one_graph_launch(spd):
+    specs, planes, off = [], [], 0
+    for sp, dec, widths in synth.batched_ranges(1.0, device=DEV):
+        specs.append(spd.RangeSpec(sp.data, widths, 7.0, dm_offset=off, decimation=dec))
+        planes.append((sp.data, widths, off))
+        off += sp.n_dm
+    cap = 1 << 24
+    bs = spd.BatchedSearch(specs, cap, tuning={"ctas_per_sm": 0, "group_scale": 1}, graph=True)
+    bs.run()
+    count, status = spd.read_result(bs.result)
+    assert status == 0 and 0 < count < cap
+    gm = spd.msd_to_numpy(bs.msd)
+    rng = np.random.default_rng(2025)
+    recs_dev = bs.out[:count]
+    for k, (x, widths, dm_off) in enumerate(planes):
+        op = oracle.Plane(synth.to_host_numpy(x))
+        mean, sd = oracle.plane_msd(op)
+        P.check_msd(gm[k:k + 1], mean, sd)
+        # rows with a candidate, and random rows
+        dms = recs_dev[(recs_dev[:, 0] >= dm_off) & (recs_dev[:, 0] < dm_off + x.shape[0]), 0]
+        hit = (torch.unique(dms) - dm_off).cpu().numpy()
+        rows = list(rng.choice(hit, size=min(2, len(hit)), replace=False)) + \
+            list(rng.choice(x.shape[0], size=1))
+        _check_rows(op, recs_dev, rows, dm_off, widths, float(mean[0]), float(sd[0]), 7.0, rng,
+                    n_cand=60, n_pos=80)
+        del op
