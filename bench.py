@@ -87,9 +87,9 @@ def detect_source_sha() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic(n_samples: int, n_cand: int):
-    """DRAM bytes per detect launch from the committed ncu summary, scaled to
-    this launch; None when absent or taken on a different kernel source."""
+def _recorded():
+    """The committed ncu record of one detect launch, or None when absent or
+    taken on a different kernel source."""
     try:
         kv = {}
         with open(TRAFFIC_FILE) as f:
@@ -97,13 +97,29 @@ def recorded_traffic(n_samples: int, n_cand: int):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256") != detect_source_sha():
-            return None
-        read = float(kv["dram_read_bytes"]) * n_samples / float(kv["samples"])
-        write = float(kv["dram_write_bytes"]) * max(n_cand, 1) / max(float(kv["candidates"]), 1)
-        return int(read + write)
-    except Exception:
+        return kv if kv.get("kernel_source_sha256") == detect_source_sha() else None
+    except OSError:
         return None
+
+
+def recorded_traffic(n_samples: int, n_cand: int):
+    """DRAM bytes per detect launch from the committed ncu record, scaled to
+    this launch (reads by samples, writes by candidates); None without one."""
+    kv = _recorded()
+    if kv is None:
+        return None
+    read = float(kv["dram_read_bytes"]) * n_samples / float(kv["samples"])
+    write = float(kv["dram_write_bytes"]) * max(n_cand, 1) / max(float(kv["candidates"]), 1)
+    return int(read + write)
+
+
+def recorded_instructions(n_samples: int):
+    """Issued warp instructions per detect launch from the committed ncu
+    record, scaled by samples (same data recipe); None without one."""
+    kv = _recorded()
+    if kv is None or "warp_instructions" not in kv:
+        return None
+    return float(kv["warp_instructions"]) * n_samples / float(kv["samples"])
 
 
 class Clocks:
@@ -153,6 +169,32 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+SM_COUNT, SCHEDULERS_PER_SM = 152, 4
+
+
+def issue_roofline(n_samples: int, det_ms: float):
+    """The bound the detect kernel actually meets: instruction issue.  achieved
+    = recorded warp instructions (ncu, scaled to this launch) / the live
+    CUDA-event time; peak = one warp instruction per scheduler per cycle at the
+    measured maximum SM clock."""
+    inst = recorded_instructions(n_samples)
+    mhz = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = json.load(f).get("sm_max_mhz")
+    except (OSError, ValueError):
+        pass
+    mhz = mhz or 2070.0
+    peak = SM_COUNT * SCHEDULERS_PER_SM * mhz * 1e6 / 1e12      # T warp-instr/s
+    if inst is None:
+        return {"bound": "issue", "achieved": None, "peak": peak, "unit": "Twarp-inst/s",
+                "frac": None, "note": "no ncu record for this kernel source"}
+    ach = inst / (det_ms / 1e3) / 1e12
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "Twarp-inst/s",
+            "frac": ach / peak, "warp_instructions": inst,
+            "peak_source": f"{SM_COUNT} SMs x {SCHEDULERS_PER_SM} schedulers x {mhz:.0f} MHz"}
 
 
 def workload_config(n_dm, n_samp, world):
@@ -302,6 +344,7 @@ def run_spd(a, rank, world, local):
                          "frac": achieved / hbm, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "algorithmic_bytes": det_bytes, "ms": det_ms},
+            "issue_roofline": issue_roofline(n, det_ms),
             "step_breakdown_ms": {"msd": msd_ms, "detect": det_ms},
             "whole_step_hbm_frac": (2 * n * 4 + 16 * count) / (ms_step / 1e3) / 1e9 / hbm,
             "gpu_launches": KERNELS_PER_STEP * a.steps,
