@@ -46,10 +46,15 @@ class ShardedSearch:
     x: this rank's rows (device tensor or binding.Plane); dm_offset: its first
     DM row in the whole plane; gather: the all-gather of a partial (default
     :func:`allgather_parts` over `group`).  run() issues partial, exchange,
-    merge and the fused detect on the current stream."""
+    merge and the fused detect on the current stream.
+
+    msd_slots > 1 keeps that many MSD states (partials, merged MSD, MSD
+    workspace) apart from the detect workspace, so that the MSD of the next
+    plane (msd_step(slot=1)) may run on another stream while detect_step(0)
+    searches with slot 0's MSD."""
 
     def __init__(self, x, widths, threshold, capacity, *, dm_offset=0, sigma_mode=0,
-                 nmax_sigma=0, group=None, gather=None, workspace=None):
+                 nmax_sigma=0, group=None, gather=None, msd_slots=1):
         import torch
 
         from . import binding as b
@@ -65,32 +70,39 @@ class ShardedSearch:
         dev = self.pl.data.device
         lib = b.load()
         cp = self.pl.c()
-        need = max(lib.spd_msd_workspace_bytes(cp, b.MSD_GLOBAL, self.nmax),
-                   b.search_workspace_bytes(self.pl, self.widths, self.threshold,
-                                            self.sigma_mode, b.MSD_GLOBAL, self.nmax))
-        self.ws = workspace if workspace is not None else b._workspace(need, dev)
-        self.part = torch.empty(b.PART_BYTES, dtype=torch.uint8, device=dev)
-        self.npart = torch.empty(b.PART_BYTES, dtype=torch.uint8, device=dev)
-        self.msd = torch.empty(b.MSD_BYTES, dtype=torch.uint8, device=dev)
+        prm, keep = b._params(self.widths, self.threshold, self.sigma_mode, b.MSD_GLOBAL,
+                              self.nmax)
+        msd_ws = lib.spd_msd_workspace_bytes(cp, b.MSD_GLOBAL, self.nmax)
+        det_ws = lib.spd_detect_workspace_bytes(cp, prm)
+        self.ws_det = b._workspace(det_ws, dev)
+        self.slots = []
+        for _ in range(max(1, int(msd_slots))):
+            self.slots.append({
+                "part": torch.empty(b.PART_BYTES, dtype=torch.uint8, device=dev),
+                "npart": torch.empty(b.PART_BYTES, dtype=torch.uint8, device=dev),
+                "msd": torch.empty(b.MSD_BYTES, dtype=torch.uint8, device=dev),
+                "ws": b._workspace(msd_ws, dev)})
+        self.msd = self.slots[0]["msd"]
         self.out = torch.empty((max(self.capacity, 1), 4), dtype=torch.int32, device=dev)
         self.result = torch.zeros(b.RESULT_BYTES, dtype=torch.uint8, device=dev)
 
-    def msd_step(self):
-        b = self.b
-        b.msd_shard_partial(self.pl, out=self.part, workspace=self.ws)
-        parts = self.gather(self.part)
-        b.msd_merge_partials(parts, parts.numel() // b.PART_BYTES, out=self.msd)
+    def msd_step(self, slot=0):
+        b, st = self.b, self.slots[slot]
+        b.msd_shard_partial(self.pl, out=st["part"], workspace=st["ws"])
+        parts = self.gather(st["part"])
+        b.msd_merge_partials(parts, parts.numel() // b.PART_BYTES, out=st["msd"])
         if self.sigma_mode:
-            b.sd_nmax_shard_partial(self.pl, self.nmax, self.msd, out=self.npart,
-                                    workspace=self.ws)
-            nparts = self.gather(self.npart)
-            b.sd_nmax_merge_partials(nparts, nparts.numel() // b.PART_BYTES, self.nmax, self.msd)
-        return self.msd
+            b.sd_nmax_shard_partial(self.pl, self.nmax, st["msd"], out=st["npart"],
+                                    workspace=st["ws"])
+            nparts = self.gather(st["npart"])
+            b.sd_nmax_merge_partials(nparts, nparts.numel() // b.PART_BYTES, self.nmax,
+                                     st["msd"])
+        return st["msd"]
 
-    def detect_step(self):
-        return self.b.detect(self.pl, self.msd, self.widths, self.threshold, self.capacity,
-                             self.sigma_mode, self.b.MSD_GLOBAL, self.nmax, out=self.out,
-                             result=self.result, workspace=self.ws)
+    def detect_step(self, slot=0):
+        return self.b.detect(self.pl, self.slots[slot]["msd"], self.widths, self.threshold,
+                             self.capacity, self.sigma_mode, self.b.MSD_GLOBAL, self.nmax,
+                             out=self.out, result=self.result, workspace=self.ws_det)
 
     def run(self):
         self.msd_step()
