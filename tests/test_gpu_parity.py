@@ -110,6 +110,16 @@ def test_width_programs(spd, widths):
     _full_case(spd, sp.data, sp.n_samp, widths, 7.0)
 
 
+@pytest.mark.parametrize("widths", [list(range(1, 4097)), list(range(8, 4097, 8))])
+def test_maximum_width_lists(spd, widths):
+    """The API's limits: all 4096 widths (the largest group scale, 64 groups,
+    plane output packed over 64 blocks of widths) and 512 coarse widths up to
+    SPD_MAX_WIDTH, on rows a little longer than the widest window."""
+    sp = synth.ska_like(2, 9000, n_pulses=3, device=DEV, seed=4096 + len(widths),
+                        fwhm_range=(1.0, 1500.0))
+    _full_case(spd, sp.data, sp.n_samp, widths, 7.0)
+
+
 def test_ska_like_small(spd):
     """The SKA-like recipe (drift + Gaussian pulses) at reduced size, config widths."""
     widths = list(range(1, 17)) + list(range(24, 257, 8))
