@@ -116,7 +116,9 @@ typedef struct {
 /* Device-side summary written by the candidate-producing calls (16 bytes).
  * count: exact number of samples with SNR >= threshold, even when it exceeds
  * the capacity (then only `capacity` records are written, which ones is
- * unspecified); status: SPD_OK or SPD_ERR_DEGENERATE_SIGMA. */
+ * unspecified); status: SPD_OK, SPD_ERR_DEGENERATE_SIGMA, or SPD_ERR_TIMEOUT
+ * (a tile's bulk copy did not land within the kernel's wait bound, 2 s: the
+ * kernel stopped instead of waiting on; see spd_debug_set_copy_wait). */
 typedef struct {
     uint64_t count;
     int32_t status;
@@ -299,7 +301,7 @@ typedef struct {
 
 /* Launch shape of the detect kernel (what the autotuner chooses).
  * ctas_per_sm: persistent CTAs per SM, 0 = as many as fit.
- * group_scale: widths per group are 16 (step 1) or 2 (16/G + 1) (step G)
+ * group_scale: widths per group are 16 (step 1) or 4 (16/G + 1) (step G)
  *   times this factor (>= 1): larger groups mean fewer bounds and group starts,
  *   smaller groups a finer pruning of the candidate search. */
 typedef struct {
@@ -318,8 +320,8 @@ size_t spd_search_batched_workspace_bytes(const spd_range *ranges, int32_t n_ran
 /* The whole path over up to SPD_MAX_RANGES DM ranges of uneven length, width
  * set and decimation: per range the MSD (a) and its constants, then ONE
  * persistent detect launch (b, c, d) whose CTAs walk the tiles of all ranges
- * -- per launch, ranges whose width lists step by the same G (8, 16 or 1);
- * ranges must share the storage type.  Every call is a fixed sequence of
+ * -- per launch, ranges whose width lists step by the same G (8, 16 or 1) and
+ * that share storage type and row alignment.  Every call is a fixed sequence of
  * asynchronous launches with no host synchronisation and no allocation, so it
  * can be captured in a CUDA graph and replayed.
  *   tuning: NULL for the defaults.
@@ -329,7 +331,7 @@ size_t spd_search_batched_workspace_bytes(const spd_range *ranges, int32_t n_ran
  *     (1 or n_dm entries each); NULL keeps them in the workspace.
  * Each range's records are the records spd_search gives for that range alone
  * (with dm_offset added).  Errors: as spd_search; SPD_ERR_INVALID_ARG for
- * n_ranges outside 1..SPD_MAX_RANGES or mixed storage types. */
+ * n_ranges outside 1..SPD_MAX_RANGES. */
 spd_status spd_search_batched(const spd_range *ranges, int32_t n_ranges,
                               const spd_tuning *tuning, spd_candidate *out, int64_t capacity,
                               spd_result *result_dev, spd_msd_stats *msd_out_dev,
