@@ -179,6 +179,22 @@ def ska_like(n_dm=4096, n_samp=524288, *, n_pulses=200, mean=100.0, sd=12.0,
                               f"over U{adj_range} rows"))
 
 
+def precision_plane(n_dm=4096, n_samp=524288, *, device="cpu", seed=1611_2,
+                    train_frac=0.05, train_seed=1611_3) -> tuple:
+    """The precision form's FP32 signal before storage: the SKA-like recipe plus,
+    on a seeded train_frac of the rows, a 4000-sample pulse train (125 width-8
+    top-hats every 32 samples from sample 100000, total matched SNR 200 at
+    sd 12).  Returns (SynthPlane, train rows)."""
+    sp = ska_like(n_dm, n_samp, device=device, seed=seed)
+    n_train = max(1, int(round(train_frac * n_dm)))
+    g = torch.Generator().manual_seed(train_seed)
+    rows = torch.randperm(n_dm, generator=g)[:n_train].tolist()
+    for r in rows:
+        inject_pulse_train(sp.data, r, min(100000, max(0, n_samp - 4000)), 125, 8, 32,
+                           200 * 12.0 / math.sqrt(1000), n_samp)
+    return sp, rows
+
+
 def quantise_rows(sp: SynthPlane, dtype: str, q_max: float = 16384.0) -> SynthPlane:
     """Store a float32 plane as FP16 or BF16 with an FP32 per-row scale
     scale_r = max|x_r| / q_max (offset 0); the stored value is round(x / scale)."""
