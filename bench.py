@@ -435,8 +435,9 @@ def run_other(a):
     import paper_1611_09704_gb300 as spd
     import synth
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(local)
     spd.build()
     spd.load()
     hbm, peak_kind = peaks()
@@ -646,6 +647,9 @@ def run_serving(a, spd, synth, line, dev):
 def main():
     a = parse()
     if a.workload != "ska" and a.impl == "spd":
+        # single-GPU measurements: under torchrun, rank 0 alone runs them
+        if int(os.environ.get("RANK", "0")) != 0:
+            return 0
         return run_other(a)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
