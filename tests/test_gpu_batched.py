@@ -63,6 +63,26 @@ def test_batched_equals_per_range_searches(spd):
     assert m.size == sum(1 if r.scope == 0 else r.x.shape[0] for r in specs)
 
 
+def test_batched_mixed_storage_types(spd):
+    """FP32, FP16 (per-row scale) and BF16 ranges in one call: one launch per
+    storage type, the same records as per-range searches."""
+    specs, off = [], 0
+    for k, dt in enumerate(("f32", "f16", "bf16")):
+        sp = synth.ska_like(6, 20000 + 3000 * k, n_pulses=4, device=DEV, seed=40 + k)
+        if dt == "f32":
+            specs.append(spd.RangeSpec(sp.data, list(range(1, 33)), 6.0, dm_offset=off))
+        else:
+            q = synth.quantise_rows(sp, dt)
+            specs.append(spd.RangeSpec(spd.Plane(q.data, scale=q.scale), list(range(1, 33)), 6.0,
+                                       dm_offset=off))
+        off += 6
+    want = _single(spd, specs)
+    out, res, _ = spd.search_batched(specs, 1_000_000)
+    c, st = spd.read_result(res)
+    assert st == 0 and c == want.size and c > 0
+    assert np.array_equal(_key(spd.candidates_to_numpy(out, c)), want)
+
+
 @pytest.mark.parametrize("tuning", [{"ctas_per_sm": 1, "group_scale": 2},
                                     {"ctas_per_sm": 0, "group_scale": 4}])
 def test_batched_graph_replays(spd, tuning):
