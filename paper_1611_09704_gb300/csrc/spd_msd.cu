@@ -1,10 +1,12 @@
 // spd_msd.cu -- step (a): mean and standard deviation of the DM x time plane
 // (Sec. 2.1).  Two kernels, as the paper splits them:
 //   msd_partial_kernel: every block reduces one equal-sized unit of a row
-//     (kMsdUnit samples) to (n, T, S).  Each thread applies Eq. 1 to groups of
-//     four consecutive samples and Eq. 2 to fold each group into its running
-//     (n, T, S); lanes, then warps, are folded with Eq. 2.  FP32 throughout,
-//     with T carried as an unevaluated hi + lo pair (compensated summation).
+//     (kMsdUnit samples) to (n, T, S).  Each thread takes 16 consecutive
+//     samples at a time as two sets of 8 (even and odd positions) in the two
+//     lanes of packed f32x2 arithmetic, applies Eq. 1 to each set and Eq. 2 to
+//     fold it into the lane's running (n, T, S); the two lanes, then lanes of
+//     the warp, then warps, are folded with Eq. 2.  FP32 throughout, with T
+//     carried as an unevaluated hi + lo pair (compensated summation).
 //   msd_merge_*: Eq. 2 over the unit partials in FP64 in a fixed tree order
 //     (deterministic), giving mu = T/n and sigma = sqrt(S/n) (population sd).
 // Plus the per-width constant kernel of step (c): 1/sigma_w from Eq. 4 / 5.
@@ -23,11 +25,6 @@ struct Acc {
     __device__ __forceinline__ Acc()
         : m(0.f), Th(0.f), Tl(0.f), S(0.f), lo(INFINITY), hi(-INFINITY) {}
 
-    __device__ __forceinline__ void range4(float a, float b, float c, float d) {
-        lo = fminf(lo, fminf(fminf(a, b), fminf(c, d)));
-        hi = fmaxf(hi, fmaxf(fmaxf(a, b), fmaxf(c, d)));
-    }
-
     // TwoSum: Th + v exactly as (Th, error) -> error folded into Tl.
     __device__ __forceinline__ void add_T(float v) {
         const float s = Th + v;
@@ -35,34 +32,6 @@ struct Acc {
         const float e = (Th - (s - bb)) + (v - bb);
         Th = s;
         Tl += e;
-    }
-
-    // Eq. 2 with the second set holding n = 4 samples of sum tb and S sb.
-    __device__ __forceinline__ void fold4(float tb, float sb) {
-        if (m == 0.f) {
-            Th = tb; Tl = 0.f; S = sb; m = 4.f;
-            return;
-        }
-        const float ta = Th + Tl;
-        const float q = __fdividef(1.f, m * (m + 4.f));
-        const float f = (4.f * (m + 4.f) * q) * ta - tb;         // (n/m) T_a - T_b
-        S += sb + (0.25f * m * m * q) * f * f;                   // m/(n(m+n)) (...)^2
-        add_T(tb);
-        m += 4.f;
-    }
-
-    // Eq. 1 over four consecutive samples (j = 1..4), then fold with Eq. 2.
-    __device__ __forceinline__ void add4(float a, float b, float c, float d) {
-        const float t2 = a + b;
-        const float d2 = fmaf(2.f, b, -t2);
-        float s = 0.5f * d2 * d2;
-        const float t3 = t2 + c;
-        const float d3 = fmaf(3.f, c, -t3);
-        s = fmaf(d3 * d3, 1.f / 6.f, s);
-        const float t4 = t3 + d;
-        const float d4 = fmaf(4.f, d, -t4);
-        s = fmaf(d4 * d4, 1.f / 12.f, s);
-        fold4(t4, s);
     }
 
     // Eq. 1 for a single further sample x_j, j = m + 1.
@@ -107,33 +76,125 @@ struct Acc {
     }
 };
 
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// Running (n, T, S) of two disjoint sets of equal size n, one per lane of a
+// float2, updated with packed f32x2 arithmetic; T = Th + Tl per lane.
+struct Acc2 {
+    float m;
+    float2 Th, Tl, S;
+
+    __device__ __forceinline__ Acc2() : m(0.f), Th(f2(0.f)), Tl(f2(0.f)), S(f2(0.f)) {}
+
+    // Eq. 1 over v[0..7] (one set of 8 per lane): returns U = -T_8 and S_8.
+    // The j-th term uses (j - 1) x_j - T_{j-1}, which equals j x_j - T_j.
+    static __device__ __forceinline__ void eq1_8(const float2 *v, float2 &U, float2 &S8) {
+        const float2 m1 = f2(-1.f);
+        U = __fmul2_rn(v[0], m1);
+        float2 d = __fadd2_rn(v[1], U);
+        S8 = __fmul2_rn(__fmul2_rn(d, f2(1.f / 2.f)), d);
+        U = __ffma2_rn(v[1], m1, U);
+#pragma unroll
+        for (int j = 3; j <= 8; ++j) {
+            d = __ffma2_rn(v[j - 1], f2((float)(j - 1)), U);
+            S8 = __ffma2_rn(__fmul2_rn(d, f2(1.f / (float)(j * (j - 1)))), d, S8);
+            U = __ffma2_rn(v[j - 1], m1, U);
+        }
+    }
+
+    // (T, S) of v[0..7] per lane by their definition: the sum, then the
+    // squared deviations from the group mean.  Returns U = -T and S8.
+    static __device__ __forceinline__ void direct_8(const float2 *v, float2 &U, float2 &S8) {
+        const float2 t = __fadd2_rn(__fadd2_rn(__fadd2_rn(v[0], v[1]), __fadd2_rn(v[2], v[3])),
+                                    __fadd2_rn(__fadd2_rn(v[4], v[5]), __fadd2_rn(v[6], v[7])));
+        const float2 nm = __fmul2_rn(t, f2(-0.125f));   // minus the mean
+        float2 d = __fadd2_rn(v[0], nm);
+        S8 = __fmul2_rn(d, d);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            d = __fadd2_rn(v[k], nm);
+            S8 = __ffma2_rn(d, d, S8);
+        }
+        U = __fmul2_rn(t, f2(-1.f));
+    }
+
+    // Eq. 2: fold a set of 8 per lane (sum -U, S8) into the running sets.
+    __device__ __forceinline__ void fold8(float2 U, float2 S8) {
+        const float2 m1 = f2(-1.f);
+        if (m == 0.f) {
+            Th = __fmul2_rn(U, m1);
+            Tl = f2(0.f);
+            S = S8;
+            m = 8.f;
+            return;
+        }
+        const float q = __fdividef(1.f, m * (m + 8.f));
+        const float r = 8.f * (m + 8.f) * q;          // n / m
+        const float k = 0.125f * m * m * q;           // m / (n (m + n))
+        const float2 ta = __fadd2_rn(Th, Tl);
+        const float2 f = __ffma2_rn(f2(r), ta, U);    // (n/m) T_a - T_b
+        S = __ffma2_rn(__fmul2_rn(f, f), f2(k), __fadd2_rn(S, S8));
+        // TwoSum: Th + T_b exactly as (s, e), T_b = -U
+        const float2 sm = __ffma2_rn(U, m1, Th);
+        const float2 bb = __ffma2_rn(Th, m1, sm);
+        const float2 t2 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, Th);
+        const float2 e = __ffma2_rn(__fadd2_rn(U, bb), m1, t2);
+        Th = sm;
+        Tl = __fadd2_rn(Tl, e);
+        m += 8.f;
+    }
+
+    // Eq. 2: the two lanes as one scalar accumulator.
+    __device__ __forceinline__ Acc lanes() const {
+        Acc a, b;
+        a.m = m; a.Th = Th.x; a.Tl = Tl.x; a.S = S.x;
+        b.m = m; b.Th = Th.y; b.Tl = Tl.y; b.S = S.y;
+        a.merge(b.m, b.Th, b.Tl, b.S);
+        return a;
+    }
+};
+
+// 16 consecutive samples as 8 float2: v[k] = (x[2k], x[2k+1]).
 template <int DT>
-__device__ __forceinline__ void load4(const typename Elem<DT>::T *p, float &a, float &b,
-                                      float &c, float &d);
-
-template <>
-__device__ __forceinline__ void load4<SPD_F32>(const float *p, float &a, float &b, float &c,
-                                               float &d) {
-    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
-    a = v.x; b = v.y; c = v.z; d = v.w;
-}
-
-template <>
-__device__ __forceinline__ void load4<SPD_F16>(const __half *p, float &a, float &b, float &c,
-                                               float &d) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p));
-    const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
-    const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
-    a = lo.x; b = lo.y; c = hi.x; d = hi.y;
-}
-
-template <>
-__device__ __forceinline__ void load4<SPD_BF16>(const __nv_bfloat16 *p, float &a, float &b,
-                                                float &c, float &d) {
-    const uint2 v = __ldcs(reinterpret_cast<const uint2 *>(p));
-    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
-    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
-    a = lo.x; b = lo.y; c = hi.x; d = hi.y;
+__device__ __forceinline__ void load16(const typename Elem<DT>::T *p, bool vec, float2 *v) {
+    if (vec) {
+        if constexpr (DT == SPD_F32) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 f = __ldcs(reinterpret_cast<const float4 *>(p) + q);
+                v[2 * q] = make_float2(f.x, f.y);
+                v[2 * q + 1] = make_float2(f.z, f.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p) + q);
+                if constexpr (DT == SPD_F16) {
+                    v[2 * q] = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+                    v[2 * q + 1] = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+                } else {
+                    v[2 * q] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+                    v[2 * q + 1] =
+                        __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = make_float2(Elem<DT>::cvt(p[2 * k]), Elem<DT>::cvt(p[2 * k + 1]));
+    }
 }
 
 template <int DT>
@@ -149,26 +210,31 @@ __global__ void __launch_bounds__(kMsdThreads) msd_partial_kernel(const MsdArgs 
     const float sc = has_sc ? a.scale[row] : 1.f;
     const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
 
-    Acc acc;
-    const int64_t ngrp = len >> 2;
+    // 16 samples per thread and step: Eq. 1 on the even and on the odd eight
+    // (one per f32x2 lane), Eq. 2 into the lane's running partial
+    Acc2 acc2;
+    float lo = INFINITY, hi = -INFINITY;
+    const int64_t ngrp = len >> 4;
     for (int64_t g = tid; g < ngrp; g += kMsdThreads) {
-        float x0, x1, x2, x3;
-        if (a.vec_ok) {
-            load4<DT>(p + 4 * g, x0, x1, x2, x3);
-        } else {
-            x0 = Elem<DT>::cvt(p[4 * g]);
-            x1 = Elem<DT>::cvt(p[4 * g + 1]);
-            x2 = Elem<DT>::cvt(p[4 * g + 2]);
-            x3 = Elem<DT>::cvt(p[4 * g + 3]);
-        }
+        float2 v[8];
+        load16<DT>(p + 16 * g, a.vec_ok != 0, v);
         if (has_sc) {
-            x0 = fmaf(sc, x0, of); x1 = fmaf(sc, x1, of);
-            x2 = fmaf(sc, x2, of); x3 = fmaf(sc, x3, of);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ffma2_rn(f2(sc), v[k], f2(of));
         }
-        acc.range4(x0, x1, x2, x3);
-        acc.add4(x0, x1, x2, x3);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            lo = fmin3(lo, v[k].x, v[k].y);
+            hi = fmax3(hi, v[k].x, v[k].y);
+        }
+        float2 U, S8;
+        Acc2::eq1_8(v, U, S8);
+        acc2.fold8(U, S8);
     }
-    for (int64_t t = 4 * ngrp + tid; t < len; t += kMsdThreads) {
+    Acc acc = acc2.lanes();
+    acc.lo = lo;
+    acc.hi = hi;
+    for (int64_t t = 16 * ngrp + tid; t < len; t += kMsdThreads) {
         float x = Elem<DT>::cvt(p[t]);
         if (has_sc) x = fmaf(sc, x, of);
         acc.add1(x);
@@ -323,20 +389,61 @@ __global__ void __launch_bounds__(256) consts_kernel(const ConstArgs a,
 
 // ----------------------------------------------------- sigma_Nmax (Eq. 5)
 
-constexpr int kNmaxTile = 4096;        // start samples of one tile
-constexpr int kNmaxPer = kNmaxTile / kMsdThreads;   // 16 consecutive starts per thread
-constexpr int kNmaxTilesPerCta = 8;    // consecutive tiles of one row per CTA (one partial)
+constexpr int kNmaxThreads = 128;
+constexpr int kNmaxPer = 64;                                // consecutive starts per thread
+constexpr int kNmaxTile = kNmaxThreads * kNmaxPer;          // 8192 starts per tile
+constexpr int kNmaxTilesPerCta = 4;    // consecutive tiles of one row per CTA (one partial)
+
+// Four stored samples as one load, and their values as two float2.
+template <int DT> struct Quad;
+template <> struct Quad<SPD_F32> {
+    using V = float4;
+    static constexpr int kInFlight = 9;   // loads in flight per thread while staging
+    static __device__ __forceinline__ V ld(const float *p) {
+        return __ldcs(reinterpret_cast<const float4 *>(p));
+    }
+    static __device__ __forceinline__ void cvt(V v, float2 &a, float2 &b) {
+        a = make_float2(v.x, v.y);
+        b = make_float2(v.z, v.w);
+    }
+};
+template <> struct Quad<SPD_F16> {
+    using V = uint2;
+    static constexpr int kInFlight = 17;
+    static __device__ __forceinline__ V ld(const __half *p) {
+        return __ldcs(reinterpret_cast<const uint2 *>(p));
+    }
+    static __device__ __forceinline__ void cvt(V v, float2 &a, float2 &b) {
+        a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+        b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    }
+};
+template <> struct Quad<SPD_BF16> {
+    using V = uint2;
+    static constexpr int kInFlight = 17;
+    static __device__ __forceinline__ V ld(const __nv_bfloat16 *p) {
+        return __ldcs(reinterpret_cast<const uint2 *>(p));
+    }
+    static __device__ __forceinline__ void cvt(V v, float2 &a, float2 &b) {
+        a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+        b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+    }
+};
 
 // Sec. 2.2, Eq. 5 needs sigma_Nmax, the measured sd of the boxcar series
 // B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA walks up
 // to kNmaxTilesPerCta consecutive tiles of one row; per tile it stages the
-// centred samples plus an (Nmax - 1)-sample halo and forms B for its 16
-// consecutive starts per thread (whole-block sums plus partial sums for the
-// first start, then sliding one sample), adding them with Eq. 1 to the
-// thread's running (n, T, S).  At the end Eq. 2 merges across lanes and warps
-// into the CTA's one partial.  The sd does not depend on the centring.
+// centred samples plus an (Nmax - 1)-sample halo, with 16-sample block sums.
+// A thread owns 64 consecutive starts: B at the first from the whole blocks
+// of its window (four interleaved sums) plus the partial block, then sliding
+// one sample at a time.  Per 16 starts, the even and the odd eight (one per
+// f32x2 lane) give (n, T, S) directly (sum, then squared deviations from
+// their mean), and Eq. 2 folds each into the lane's running (n, T, S); starts
+// near the row end take Eq. 1 one at a time.  At the end
+// Eq. 2 merges the lanes, then lanes of the warp and warps, into the CTA's
+// one partial.  The sd does not depend on the centring.
 template <int DT>
-__global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArgs a) {
+__global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const NmaxArgs a) {
     using T = typename Elem<DT>::T;
     // centred samples, 16 positions in 20 words (lane t reading 16t + k with
     // 128-bit loads hits distinct banks within each quarter warp)
@@ -349,39 +456,66 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArg
     const int64_t tl0 = part * kNmaxTilesPerCta;
     const int64_t tl1 = min(tl0 + kNmaxTilesPerCta, tiles_in_row);
     const int entry = a.per_row ? (int)row : 0;
-    const double mu = a.msd[entry].mean;
-    const float mh = (float)mu, ml = (float)(mu - (double)mh);
     const T *rp = static_cast<const T *>(a.data) + row * a.stride;
     const bool has_sc = a.scale != nullptr;
     const float sc = has_sc ? a.scale[row] : 1.f;
     const float of = (has_sc && a.offset) ? a.offset[row] : 0.f;
+    // centring shift, rounded once: a constant error in it moves every B of
+    // the row alike, which the sd does not see
+    const float cy = (float)((double)of - a.msd[entry].mean);
+    const float2 sc2 = f2(sc), c2 = f2(cy);
+    constexpr int kQ = Quad<DT>::kInFlight;
     const int nmax = a.nmax;
-    const int p0 = tid * kNmaxPer;                 // first start of this thread (tile-local)
-    const int qe = p0 + nmax;
-    Acc acc;
+    const int b0 = tid * (kNmaxPer / 16);          // the thread's first block (tile-local)
+    const int qe = 16 * b0 + nmax;                 // end of its first window
+    Acc2 acc2;      // full 16-start units
+    Acc tail_acc;   // starts near the row end
     for (int64_t tl = tl0; tl < tl1; ++tl) {
         const int64_t t0 = tl * (int64_t)kNmaxTile;
         __syncthreads();   // the previous tile's reads of s_y / s_bs are done
-        for (int q4 = tid; q4 < 4 * a.nb; q4 += kMsdThreads) {
-            const int p = 4 * q4;
-            float x[4];
-            if (a.vec_ok && t0 + p + 3 < a.n_samp) {
-                load4<DT>(rp + t0 + p, x[0], x[1], x[2], x[3]);
+        // Stage the window, kQ groups of 4 samples per thread at a time: all
+        // loads of a round are issued before any is used, so a tile waits for
+        // memory once per round.  y = scale x + (offset - mu), one rounding;
+        // positions past the row end hold 0.
+        const int nq = 4 * a.nb;
+        for (int c0 = 0; c0 < nq; c0 += kQ * kNmaxThreads) {
+            const int cq = min(c0 + kQ * kNmaxThreads, nq);   // this round's end
+            if (a.vec_ok && t0 + 4 * (int64_t)cq <= a.n_samp) {
+                typename Quad<DT>::V r[kQ];
+#pragma unroll
+                for (int u = 0; u < kQ; ++u) {
+                    const int q4 = c0 + u * kNmaxThreads + tid;
+                    if (q4 < cq) r[u] = Quad<DT>::ld(rp + t0 + 4 * q4);
+                }
+#pragma unroll
+                for (int u = 0; u < kQ; ++u) {
+                    const int q4 = c0 + u * kNmaxThreads + tid;
+                    if (q4 < cq) {
+                        float2 v0, v1;
+                        Quad<DT>::cvt(r[u], v0, v1);
+                        v0 = __ffma2_rn(sc2, v0, c2);
+                        v1 = __ffma2_rn(sc2, v1, c2);
+                        const int p = 4 * q4;
+                        *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+                            make_float4(v0.x, v0.y, v1.x, v1.y);
+                    }
+                }
             } else {
+                for (int q4 = c0 + tid; q4 < cq; q4 += kNmaxThreads) {
+                    const int p = 4 * q4;
+                    float y[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    x[e] = t0 + p + e < a.n_samp ? Elem<DT>::cvt(rp[t0 + p + e]) : 0.f;
+                    for (int e = 0; e < 4; ++e) {
+                        const int64_t t = t0 + p + e;
+                        y[e] = t < a.n_samp ? fmaf(sc, Elem<DT>::cvt(rp[t]), cy) : 0.f;
+                    }
+                    *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+                        make_float4(y[0], y[1], y[2], y[3]);
+                }
             }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (has_sc) x[e] = fmaf(sc, x[e], of);
-                x[e] = t0 + p + e < a.n_samp ? (x[e] - mh) - ml : 0.f;
-            }
-            *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
-                make_float4(x[0], x[1], x[2], x[3]);
         }
         __syncthreads();
-        for (int b = tid; b < a.nb; b += kMsdThreads) {
+        for (int b = tid; b < a.nb; b += kNmaxThreads) {
             float sum = 0.f;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -392,70 +526,87 @@ __global__ void __launch_bounds__(kMsdThreads) nmax_partial_kernel(const NmaxArg
         }
         __syncthreads();
 
-        // B at p0: whole blocks from p0 to p0 + nmax (Kahan), plus the partial
-        // block at the end (p0 is a multiple of 16)
-        float whole = 0.f, comp = 0.f;
-        for (int b = p0 >> 4; b < (qe >> 4); ++b) {
-            const float y = s_bs[b] - comp;
-            const float t = whole + y;
-            comp = (t - whole) - y;
-            whole = t;
+        // B at the thread's first start: whole blocks of the window (four
+        // interleaved sums), plus the partial block at its end
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+        int b = b0;
+        const int be = qe >> 4;
+        for (; b + 3 < be; b += 4) {
+            w0 += s_bs[b];
+            w1 += s_bs[b + 1];
+            w2 += s_bs[b + 2];
+            w3 += s_bs[b + 3];
         }
+        for (; b < be; ++b) w0 += s_bs[b];
         float tail = 0.f;
         for (int q = (qe & ~15); q < qe; ++q) tail += s_y[(q & 15) + 20 * (q >> 4)];
-        float B = whole + tail;
-        // the thread's 16 samples and the 16 that enter the window as it slides
-        float lo[16], hi[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * tid + 4 * q);
-            lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
-        }
-        if ((nmax & 15) == 0) {
+        float B = ((w0 + w1) + (w2 + w3)) + tail;
+        // starts t0 + 16 b0 + k are full windows while k < nvalid
+        const int64_t nvalid = a.n_samp - nmax - (t0 + 16 * b0) + 1;
+#pragma unroll 1
+        for (int c = 0; c < kNmaxPer / 16; ++c) {
+            // the unit's 16 samples and the 16 that enter the window as it slides
+            const int bl = b0 + c;
+            float lo[16], hi[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 f =
-                    *reinterpret_cast<const float4 *>(s_y + 20 * (tid + (nmax >> 4)) + 4 * q);
-                hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
+                const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * bl + 4 * q);
+                lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
             }
-        } else {
+            if ((nmax & 15) == 0) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int q = p0 + k + nmax;
-                hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+                for (int q = 0; q < 4; ++q) {
+                    const float4 f =
+                        *reinterpret_cast<const float4 *>(s_y + 20 * (bl + (nmax >> 4)) + 4 * q);
+                    hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int q = 16 * bl + k + nmax;
+                    hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+                }
             }
-        }
-        float bw[16];
+            // B slides by hi - lo per start (the differences as f32x2 pairs)
+            float2 bw[8];   // bw[k] = (B at unit start + 2k, B at unit start + 2k + 1)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            bw[k] = B;
-            B = (B - lo[k]) + hi[k];
-        }
-        // starts t0 + p0 + k are full windows while t0 + p0 + k + nmax <= n_samp
-        const int64_t nvalid = a.n_samp - nmax - (t0 + p0) + 1;
-        if (nvalid >= 16) {
+            for (int k = 0; k < 8; ++k) {
+                const float2 dl = __ffma2_rn(make_float2(lo[2 * k], lo[2 * k + 1]), f2(-1.f),
+                                             make_float2(hi[2 * k], hi[2 * k + 1]));
+                bw[k].x = B;
+                B += dl.x;
+                bw[k].y = B;
+                B += dl.y;
+            }
+            const int64_t nv = nvalid - 16 * c;
+            if (nv >= 16) {
+                // (T, S) of the even and of the odd eight, Eq. 2 into the lanes
+                float2 U, S8;
+                Acc2::direct_8(bw, U, S8);
+                acc2.fold8(U, S8);
+            } else {
 #pragma unroll
-            for (int k = 0; k < 16; k += 4) acc.add4(bw[k], bw[k + 1], bw[k + 2], bw[k + 3]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                if (k < nvalid) acc.add1(bw[k]);
+                for (int k = 0; k < 16; ++k)
+                    if (k < nv) tail_acc.add1(k & 1 ? bw[k >> 1].y : bw[k >> 1].x);
+            }
         }
     }
+    Acc acc = acc2.lanes();
+    acc.merge(tail_acc.m, tail_acc.Th, tail_acc.Tl, tail_acc.S);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc.merge_down(off);
-    __shared__ float4 s_w[kMsdThreads / 32];
+    __shared__ float4 s_w[kNmaxThreads / 32];
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) s_w[warp] = make_float4(acc.m, acc.Th, acc.Tl, acc.S);
     __syncthreads();
     if (warp == 0) {
         Acc b;
-        if (lane < kMsdThreads / 32) {
+        if (lane < kNmaxThreads / 32) {
             const float4 v = s_w[lane];
             b.m = v.x; b.Th = v.y; b.Tl = v.z; b.S = v.w;
         }
 #pragma unroll
-        for (int off = 4; off > 0; off >>= 1) b.merge_down(off);
+        for (int off = kNmaxThreads / 64; off > 0; off >>= 1) b.merge_down(off);
         if (lane == 0) {
             MsdPart out;
             out.n = (double)b.m;
@@ -592,10 +743,24 @@ cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
     if (tiles <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.nb * 21 * sizeof(float);
+    // above 48 KB (Nmax > 1024) the kernels opt in to the larger window
+    static const cudaError_t opt_in = [] {
+        const int most = (int)((size_t)nmax_blocks(SPD_MAX_WIDTH) * 21 * sizeof(float));
+        cudaError_t e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_F32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_F16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_BF16>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+        return e;
+    }();
+    if (opt_in != cudaSuccess) return opt_in;
     switch (dtype) {
-        case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
-        case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
-        default: nmax_partial_kernel<SPD_BF16><<<(unsigned)tiles, kMsdThreads, smem, s>>>(a); break;
+        case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kNmaxThreads, smem, s>>>(a); break;
+        case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kNmaxThreads, smem, s>>>(a); break;
+        default: nmax_partial_kernel<SPD_BF16><<<(unsigned)tiles, kNmaxThreads, smem, s>>>(a); break;
     }
     return cudaGetLastError();
 }
