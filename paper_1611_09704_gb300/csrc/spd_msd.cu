@@ -430,6 +430,24 @@ template <> struct Quad<SPD_BF16> {
     }
 };
 
+// Shared layout of the staged window: position p at word p + 4 (p / 64), so
+// 16-position blocks are contiguous and 64-position runs start 68 words apart.
+__host__ __device__ __forceinline__ int npad(int p) { return p + 4 * (p >> 6); }
+__host__ __device__ __forceinline__ int nmax_ywords(int nb) {
+    return (npad(16 * nb) + 3) & ~3;   // block sums follow, 16-byte aligned
+}
+size_t nmax_smem_bytes(int nb) { return ((size_t)nmax_ywords(nb) + nb) * sizeof(float); }
+
+__device__ __forceinline__ float block_sum(const float *s_y, int b) {
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 f = *reinterpret_cast<const float4 *>(s_y + npad(16 * b) + 4 * q);
+        sum += (f.x + f.y) + (f.z + f.w);
+    }
+    return sum;
+}
+
 // Sec. 2.2, Eq. 5 needs sigma_Nmax, the measured sd of the boxcar series
 // B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA walks up
 // to kNmaxTilesPerCta consecutive tiles of one row; per tile it stages the
@@ -445,10 +463,11 @@ template <> struct Quad<SPD_BF16> {
 template <int DT>
 __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const NmaxArgs a) {
     using T = typename Elem<DT>::T;
-    // centred samples, 16 positions in 20 words (lane t reading 16t + k with
-    // 128-bit loads hits distinct banks within each quarter warp)
-    extern __shared__ __align__(16) float s_y[];   // [nb * 20]
-    float *s_bs = s_y + 20 * a.nb;                 // [nb] block sums
+    // centred samples, 64 positions in 68 words: lane t reading its own
+    // 64-position run (or the run nmax later) with 128-bit loads hits distinct
+    // banks within each quarter warp
+    extern __shared__ __align__(16) float s_y[];   // [nmax_ywords(nb)]
+    float *s_bs = s_y + nmax_ywords(a.nb);         // [nb] block sums
     const int tid = threadIdx.x;
     const int64_t row = blockIdx.x / a.tiles_per_row;   // tiles_per_row: partials per row
     const int64_t part = blockIdx.x - row * a.tiles_per_row;
@@ -496,7 +515,7 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
                         v0 = __ffma2_rn(sc2, v0, c2);
                         v1 = __ffma2_rn(sc2, v1, c2);
                         const int p = 4 * q4;
-                        *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+                        *reinterpret_cast<float4 *>(s_y + npad(p)) =
                             make_float4(v0.x, v0.y, v1.x, v1.y);
                     }
                 }
@@ -509,37 +528,38 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
                         const int64_t t = t0 + p + e;
                         y[e] = t < a.n_samp ? fmaf(sc, Elem<DT>::cvt(rp[t]), cy) : 0.f;
                     }
-                    *reinterpret_cast<float4 *>(s_y + (p & 15) + 20 * (p >> 4)) =
+                    *reinterpret_cast<float4 *>(s_y + npad(p)) =
                         make_float4(y[0], y[1], y[2], y[3]);
                 }
             }
         }
         __syncthreads();
-        for (int b = tid; b < a.nb; b += kNmaxThreads) {
-            float sum = 0.f;
+        // block sums: the thread's own four blocks, then the halo blocks
+        {
+            float bs4[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * b + 4 * q);
-                sum += (f.x + f.y) + (f.z + f.w);
-            }
-            s_bs[b] = sum;
+            for (int c = 0; c < 4; ++c) bs4[c] = block_sum(s_y, b0 + c);
+            *reinterpret_cast<float4 *>(s_bs + b0) = make_float4(bs4[0], bs4[1], bs4[2], bs4[3]);
+            for (int b = kNmaxTile / 16 + tid; b < a.nb; b += kNmaxThreads)
+                s_bs[b] = block_sum(s_y, b);
         }
         __syncthreads();
 
         // B at the thread's first start: whole blocks of the window (four
         // interleaved sums), plus the partial block at its end
         float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
-        int b = b0;
+        int b = b0;                      // a multiple of 4: 128-bit loads
         const int be = qe >> 4;
         for (; b + 3 < be; b += 4) {
-            w0 += s_bs[b];
-            w1 += s_bs[b + 1];
-            w2 += s_bs[b + 2];
-            w3 += s_bs[b + 3];
+            const float4 f = *reinterpret_cast<const float4 *>(s_bs + b);
+            w0 += f.x;
+            w1 += f.y;
+            w2 += f.z;
+            w3 += f.w;
         }
         for (; b < be; ++b) w0 += s_bs[b];
         float tail = 0.f;
-        for (int q = (qe & ~15); q < qe; ++q) tail += s_y[(q & 15) + 20 * (q >> 4)];
+        for (int q = (qe & ~15); q < qe; ++q) tail += s_y[npad(q)];
         float B = ((w0 + w1) + (w2 + w3)) + tail;
         // starts t0 + 16 b0 + k are full windows while k < nvalid
         const int64_t nvalid = a.n_samp - nmax - (t0 + 16 * b0) + 1;
@@ -550,21 +570,21 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
             float lo[16], hi[16];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 f = *reinterpret_cast<const float4 *>(s_y + 20 * bl + 4 * q);
+                const float4 f = *reinterpret_cast<const float4 *>(s_y + npad(16 * bl) + 4 * q);
                 lo[4 * q] = f.x; lo[4 * q + 1] = f.y; lo[4 * q + 2] = f.z; lo[4 * q + 3] = f.w;
             }
             if ((nmax & 15) == 0) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float4 f =
-                        *reinterpret_cast<const float4 *>(s_y + 20 * (bl + (nmax >> 4)) + 4 * q);
+                        *reinterpret_cast<const float4 *>(s_y + npad(16 * bl + nmax) + 4 * q);
                     hi[4 * q] = f.x; hi[4 * q + 1] = f.y; hi[4 * q + 2] = f.z; hi[4 * q + 3] = f.w;
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int q = 16 * bl + k + nmax;
-                    hi[k] = s_y[(q & 15) + 20 * (q >> 4)];
+                    hi[k] = s_y[npad(q)];
                 }
             }
             // B slides by hi - lo per start (the differences as f32x2 pairs)
@@ -742,10 +762,10 @@ int64_t nmax_tiles_per_row(int64_t n_samp) {
 cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
     if (tiles <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.nb * 21 * sizeof(float);
+    const size_t smem = nmax_smem_bytes(a.nb);
     // above 48 KB (Nmax > 1024) the kernels opt in to the larger window
     static const cudaError_t opt_in = [] {
-        const int most = (int)((size_t)nmax_blocks(SPD_MAX_WIDTH) * 21 * sizeof(float));
+        const int most = (int)nmax_smem_bytes(nmax_blocks(SPD_MAX_WIDTH));
         cudaError_t e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_F32>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         if (e == cudaSuccess)
