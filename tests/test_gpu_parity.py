@@ -245,6 +245,33 @@ def test_sigma_nmax_against_oracle(spd, nmax):
         assert np.allclose(got["sd_nmax"], want, rtol=1e-5), (got["sd_nmax"], want)
 
 
+@pytest.mark.parametrize("n_dm,n_samp,stride,nmax,dt,scope", [
+    (3, 70001, None, 48, "f32", 0),      # several partials per row; Nmax = 16 k, not 64 k
+    (3, 70001, None, 1000, "f32", 1),    # Nmax not a multiple of 16; per-row scope
+    (2, 50001, 50017, 300, "f32", 0),    # odd stride (scalar staging), NaN past the row end
+    (2, 40000, None, 4096, "bf16", 0),   # the widest window (shared memory above 48 KB)
+    (3, 33000, None, 2000, "f16", 1),    # FP16 with per-row scale and offset
+])
+def test_sigma_nmax_windows(spd, n_dm, n_samp, stride, nmax, dt, scope):
+    """MSD and sigma_Nmax against the oracle (two-pass; direct window sums) for
+    the window shapes and storage forms the tiled kernels treat apart."""
+    x = synth.noise_plane(n_dm, n_samp, 100.0, 12.0, device=DEV, seed=nmax + n_samp,
+                          stride=stride)
+    scale = offset = None
+    if dt != "f32":
+        scale = (x[:, :n_samp].abs().amax(dim=1) / 16384.0).contiguous()
+        offset = torch.linspace(-2.0, 2.0, n_dm, device=DEV, dtype=torch.float32)
+        td = torch.float16 if dt == "f16" else torch.bfloat16
+        x = (x / scale.unsqueeze(1)).to(td)
+    op = _oracle_plane(x, n_samp, scale, offset)
+    mean, sd = oracle.plane_msd(op, scope)
+    want = oracle.plane_sd_nmax(op, nmax, scope)
+    got = spd.msd_to_numpy(spd.msd(x, scope, nmax, n_samp=n_samp, scale=scale, offset=offset))
+    P.check_msd(got, mean, sd)
+    assert np.all(got["nmax"] == nmax)
+    assert np.allclose(got["sd_nmax"], want, rtol=1e-5), (got["sd_nmax"], want)
+
+
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
 def test_precision_form_eq5(spd, dt):
     """The precision form: FP16 / BF16 storage with per-row scale, 5% of rows
