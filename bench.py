@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import select
 import statistics
 import subprocess
 import sys
@@ -137,6 +138,11 @@ class Clocks:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", sel, f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            # nvidia-smi's start-up (NVML initialisation) slows the CUDA calls of
+            # this process for a while: wait for its first sample, which is then
+            # dropped, so that the timed region begins after it
+            if select.select([self.p.stdout], [], [], 10.0)[0]:
+                self.p.stdout.readline()
         except Exception:
             self.p = None
 
