@@ -763,20 +763,16 @@ cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
     if (tiles <= 0) return cudaSuccess;
     const size_t smem = nmax_smem_bytes(a.nb);
-    // above 48 KB (Nmax > 1024) the kernels opt in to the larger window
-    static const cudaError_t opt_in = [] {
-        const int most = (int)nmax_smem_bytes(nmax_blocks(SPD_MAX_WIDTH));
-        cudaError_t e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_F32>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_F16>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(nmax_partial_kernel<SPD_BF16>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        return e;
-    }();
-    if (opt_in != cudaSuccess) return opt_in;
+    // above 48 KB (Nmax > 2400 or so) the kernel opts in to the larger window,
+    // on the current device, before each such launch
+    if (smem > 48 * 1024) {
+        const void *fn = dtype == SPD_F32   ? (const void *)nmax_partial_kernel<SPD_F32>
+                         : dtype == SPD_F16 ? (const void *)nmax_partial_kernel<SPD_F16>
+                                            : (const void *)nmax_partial_kernel<SPD_BF16>;
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     switch (dtype) {
         case SPD_F32: nmax_partial_kernel<SPD_F32><<<(unsigned)tiles, kNmaxThreads, smem, s>>>(a); break;
         case SPD_F16: nmax_partial_kernel<SPD_F16><<<(unsigned)tiles, kNmaxThreads, smem, s>>>(a); break;
