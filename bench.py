@@ -156,6 +156,12 @@ class Clocks:
         except Exception:
             self.p.kill()
             out = ""
+        return self.parse(out)
+
+    @staticmethod
+    def parse(out: str):
+        """Summary of nvidia-smi CSV samples (the Q fields, no units): median SM
+        clock, highest maximum clock, and the throttle reasons seen active."""
         sm, mx, reasons = [], 0.0, set()
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
