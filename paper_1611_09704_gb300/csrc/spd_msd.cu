@@ -763,7 +763,7 @@ cudaError_t launch_nmax_partial(const NmaxArgs &a, int dtype, cudaStream_t s) {
     const int64_t tiles = a.n_dm * a.tiles_per_row;
     if (tiles <= 0) return cudaSuccess;
     const size_t smem = nmax_smem_bytes(a.nb);
-    // above 48 KB (Nmax > 2400 or so) the kernel opts in to the larger window,
+    // above 48 KB (Nmax >= 2705) the kernel opts in to the larger window,
     // on the current device, before each such launch
     if (smem > 48 * 1024) {
         const void *fn = dtype == SPD_F32   ? (const void *)nmax_partial_kernel<SPD_F32>
