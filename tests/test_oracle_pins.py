@@ -377,6 +377,54 @@ def test_search_finds_injected_tophats():
         assert abs(int(top["width"]) - p.width) <= max(2, p.width // 3)
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_search_end_to_end_against_brute_force(seed):
+    """The four steps composed, on tiny planes, against an independent numpy
+    statement of each: mean and population sd (np.mean / np.std over the
+    scope), sigma_Nmax as np.std of every full Nmax-sample window sum pooled
+    over the scope, sigma_w of Eq. 4 or Eq. 5 (both readings), Algorithm 1 by
+    brute force, and the inclusive threshold."""
+    rng = np.random.default_rng(700 + seed)
+    n_dm, n = int(rng.integers(1, 4)), int(rng.integers(12, 80))
+    x = (rng.normal(0.0, 1.0, size=(n_dm, n)) + rng.normal(0.0, 0.3, size=(n_dm, 1))
+         ).astype(np.float32)
+    x[:, int(rng.integers(0, n - 4)):][:, :4] += 3.0          # a small pulse
+    mode = seed % 3
+    scope = (seed // 3) % 2
+    widths = np.sort(rng.choice(np.arange(2, 11), size=int(rng.integers(1, 6)),
+                                replace=False)).astype(np.int32)
+    thr = 2.0
+    cands, best, win, (mean, sd, sdn, _) = oracle.search(x, widths, thr, mode, scope)
+
+    x64 = x.astype(np.float64)
+    groups = [x64] if scope == oracle.SCOPE_GLOBAL else [x64[r:r + 1] for r in range(n_dm)]
+    nmax = int(widths[-1])
+    want_b, want_w = np.zeros((n_dm, n)), np.zeros((n_dm, n), np.int64)
+    for e, g in enumerate(groups):
+        mu, s = float(np.mean(g)), float(np.std(g))
+        assert mean[e] == pytest.approx(mu, abs=1e-12) and sd[e] == pytest.approx(s, rel=1e-12)
+        if mode:
+            win_sums = np.lib.stride_tricks.sliding_window_view(g, nmax, axis=1).sum(axis=2)
+            sn = float(np.std(win_sums))
+            assert sdn[e] == pytest.approx(sn, rel=1e-10)
+        sig = {}
+        for w in [1] + list(widths):
+            if mode == 0:
+                sig[w] = math.sqrt(w) * s
+            elif mode == 1:
+                sig[w] = math.sqrt(w) * s + (w - 1) * sn / (nmax - 1)
+            else:
+                sig[w] = math.sqrt(w) * s + (w - 1) * (sn - math.sqrt(nmax) * s) / (nmax - 1)
+        rows = range(n_dm) if scope == oracle.SCOPE_GLOBAL else [e]
+        for r in rows:
+            want_b[r], want_w[r] = _brute_force(x64[r], mu, sig, widths)
+    assert np.allclose(best, want_b, rtol=1e-10, atol=1e-12)
+    assert np.array_equal(win, want_w)
+    keep = np.argwhere(want_b >= thr)
+    assert [(int(c["dm"]), int(c["sample"])) for c in cands] == [(int(r), int(i)) for r, i in keep]
+    assert np.array_equal(cands["width"], want_w[want_b >= thr])
+
+
 def test_snr_at_matches_closed_form():
     """One-pair SNR: a ramp's window sum is closed-form; past the row end NaN."""
     n, a, b = 50, 2.0, 0.5
