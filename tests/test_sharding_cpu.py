@@ -1,5 +1,6 @@
 """The multi-rank path on CPU: DM-row shards, the all-gather of Chan partials
-over a world_size-2 gloo group, the Eq. 2 merge in rank order, and the
+over gloo groups of 2 and 3 ranks, the Eq. 2 merge in rank order (and the
+second round for Eq. 5's sigma_Nmax), and the
 sharded search's orchestration (with the device calls replaced by FP64 CPU
 arithmetic, since this machine has no GPU)."""
 import os
@@ -77,10 +78,27 @@ def _fake_binding(real):
         out.copy_(torch.from_numpy(rec.view(np.uint8).copy()))
         return out
 
+    def sd_nmax_shard_partial(pl, nmax, msd, out=None, workspace=None):
+        # (n, T, S) of the shard's B_Nmax series over full windows, by definition
+        x = np.asarray(pl.data[:, :pl.n_samp].numpy(), np.float64)
+        b = np.lib.stride_tricks.sliding_window_view(x, nmax, axis=1).sum(axis=2)
+        out.copy_(_part_bytes(b))
+        return out
+
+    def sd_nmax_merge_partials(parts, n_shards, nmax, out):
+        assert parts.numel() == n_shards * real.PART_BYTES
+        _, _, sdn = _merge(parts)
+        rec = out.numpy().view(real.MSD_DTYPE).copy()
+        rec["sd_nmax"], rec["nmax"] = sdn, nmax
+        out.copy_(torch.from_numpy(rec.view(np.uint8).copy()))
+        return out
+
     def detect(pl, msd, widths, thr, cap, mode, scope, nmax, out=None, result=None,
                workspace=None):
         m = msd.numpy().view(real.MSD_DTYPE)[0]
-        tab = oracle.sigma_table(0, float(m["sd"]), widths)
+        if mode:
+            assert int(m["nmax"]) == nmax
+        tab = oracle.sigma_table(mode, float(m["sd"]), widths, float(m["sd_nmax"]), nmax)
         best, win = oracle.boxcar_snr(pl.data.numpy(), [m["mean"]], [m["sd"]], [tab], widths)
         c = oracle.threshold(best, win, thr)
         recs = np.zeros(len(c), real.CAND_DTYPE)
@@ -95,10 +113,12 @@ def _fake_binding(real):
 
     f.msd_shard_partial, f.msd_merge_partials, f.detect = (msd_shard_partial,
                                                            msd_merge_partials, detect)
+    f.sd_nmax_shard_partial, f.sd_nmax_merge_partials = (sd_nmax_shard_partial,
+                                                         sd_nmax_merge_partials)
     return f
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, mode):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -114,10 +134,11 @@ def _rank(rank, world, port, q):
         # 2. the sharded search's orchestration over the group
         widths = list(range(1, 33))
         ss = ShardedSearch(torch.from_numpy(np.ascontiguousarray(x[r0:r1])), widths, 5.0,
-                           4096, dm_offset=r0)
+                           4096, dm_offset=r0, sigma_mode=mode)
         ss.b = _fake_binding(B)
         ss.run()
-        q.put((rank, _merge(got), ss.candidates()))
+        sdn = float(ss.msd.numpy().view(B.MSD_DTYPE)[0]["sd_nmax"])
+        q.put((rank, _merge(got), sdn, ss.candidates()))
     finally:
         dist.destroy_process_group()
 
@@ -128,12 +149,14 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("world", [2])
-def test_two_gloo_ranks_match_the_whole_plane(world):
+@pytest.mark.parametrize("world,mode", [(2, 0), (2, 1), (3, 2)])
+def test_gloo_ranks_match_the_whole_plane(world, mode):
+    """Eq. 4, and Eq. 5 in both readings (the second exchange: sigma_Nmax
+    partials of the B_Nmax series, merged in rank order)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q, mode)) for r in range(world)]
     for p in procs:
         p.start()
     out = [q.get(timeout=240) for _ in range(world)]
@@ -143,13 +166,15 @@ def test_two_gloo_ranks_match_the_whole_plane(world):
     out.sort(key=lambda t: t[0])
     x = _plane()
     mu, sd = oracle.twopass(x)
-    for _, (n, m, s), _ in out:
+    want, _, _, (_, _, want_sdn, _) = oracle.search(x, list(range(1, 33)), 5.0, sigma_mode=mode)
+    for _, (n, m, s), sdn, _ in out:
         assert n == x.size
         assert m == pytest.approx(mu, rel=1e-13) and s == pytest.approx(sd, rel=1e-12)
+        if mode:
+            assert sdn == pytest.approx(float(want_sdn[0]), rel=1e-10)
     # candidates of all ranks == the one-shot search of the whole plane
-    got = np.concatenate([c for _, _, c in out])
+    got = np.concatenate([c for _, _, _, c in out])
     got.sort(order=["dm", "sample"])
-    want, *_ = oracle.search(x, list(range(1, 33)), 5.0)
     assert len(want) > 0
     assert np.array_equal(got["dm"], want["dm"]) and np.array_equal(got["sample"],
                                                                       want["sample"])
