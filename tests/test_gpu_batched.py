@@ -83,6 +83,29 @@ def test_batched_mixed_storage_types(spd):
     assert np.array_equal(_key(spd.candidates_to_numpy(out, c)), want)
 
 
+def test_batched_eq5_ranges(spd):
+    """Ranges under Eq. 5 (as printed, with the default Nmax = last width, and
+    the linear-excess reading with an explicit Nmax; one per-row) beside an
+    Eq. 4 range in one call: the same records as per-range searches."""
+    specs, off = [], 0
+    for k, (mode, scope, nmax) in enumerate([(0, 0, 0), (1, 0, 0), (2, 0, 96), (1, 1, 64)]):
+        sp = synth.ska_like(5, 24000 + 2000 * k, n_pulses=4, device=DEV, seed=60 + k)
+        synth.inject_pulse_train(sp.data, row=1, t0=3000, n_pulses=40, width=8, period=32,
+                                 amp=6.0 * 12.0, n_samp=sp.n_samp)
+        widths = list(range(1, 17)) + list(range(24, 129, 8))
+        specs.append(spd.RangeSpec(sp.data, widths, 5.0, sigma_mode=mode, scope=scope,
+                                   nmax=nmax, dm_offset=off))
+        off += 5
+    want = _single(spd, specs)
+    out, res, msd = spd.search_batched(specs, 1_000_000)
+    c, st = spd.read_result(res)
+    assert st == 0 and c == want.size and c > 0
+    assert np.array_equal(_key(spd.candidates_to_numpy(out, c)), want)
+    m = spd.msd_to_numpy(msd)
+    assert list(m["nmax"][1:3]) == [128, 96] and np.all(m["nmax"][3:] == 64)
+    assert np.all(m["sd_nmax"][1:] > 0)
+
+
 @pytest.mark.parametrize("tuning", [{"ctas_per_sm": 1, "group_scale": 2},
                                     {"ctas_per_sm": 0, "group_scale": 4}])
 def test_batched_graph_replays(spd, tuning):
