@@ -34,13 +34,14 @@ LEVELS = [(0, list(range(1, 33))), (1, list(range(17, 33))), (2, list(range(17, 
           (4, [9, 12, 16, 24, 32])]
 
 
-@pytest.mark.parametrize("dtype,n_samp", [("f32", 40000), ("f32", 33333), ("f16", 40000)])
+@pytest.mark.parametrize("dtype,n_samp", [("f32", 40000), ("f32", 33333), ("f16", 40000),
+                                          ("bf16", 36000)])
 def test_decimated_matches_oracle(spd, dtype, n_samp):
     sp = synth.ska_like(10, n_samp, n_pulses=12, mean=0.0, sd=1.0, drift_amp=0.0,
                         fwhm_range=(1.0, 400.0), device=DEV, seed=91)
     x, scale = sp.data, None
-    if dtype == "f16":
-        q = synth.quantise_rows(sp, "f16")
+    if dtype != "f32":
+        q = synth.quantise_rows(sp, dtype)
         x, scale = q.data, q.scale
     thr, cap = 6.0, 1 << 20
     out, res, msd = spd.search_decimated(x, LEVELS, thr, cap, scale=scale)

@@ -83,7 +83,7 @@ SCHEDULES = {
 
 @pytest.mark.parametrize("sched", list(SCHEDULES))
 @pytest.mark.parametrize("scope", [0, 1])
-@pytest.mark.parametrize("dtype", ["f32", "f16"])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_stream_matches_oracle_replay(spd, sched, scope, dtype):
     lengths = SCHEDULES[sched]
     n_dm, total = 12, sum(lengths)
@@ -91,8 +91,8 @@ def test_stream_matches_oracle_replay(spd, sched, scope, dtype):
                             seed=31 + scope)
     x = sp.data
     scale = None
-    if dtype == "f16":
-        sp = synth.quantise_rows(sp, "f16")
+    if dtype != "f32":
+        sp = synth.quantise_rows(sp, dtype)
         x, scale = sp.data, sp.scale
     widths = list(range(1, 17)) + list(range(24, 129, 8))
     thr = 6.0
