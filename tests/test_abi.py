@@ -188,3 +188,27 @@ def test_status_strings(lib):
     for s in range(8):
         assert lib.spd_status_string(s)
     assert lib.spd_version() >= 100
+
+
+def test_missing_library_fails_loudly():
+    """Without the built CUDA library the product raises: no CPU fallback
+    computes anything in its place."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import torch, paper_1611_09704_gb300 as spd\n"
+        "from paper_1611_09704_gb300 import builder\n"
+        "builder.LIB = '/nonexistent/libspd.so'\n"
+        "x = torch.zeros((2, 64))\n"
+        "for call in (lambda: spd.msd(x), lambda: spd.search(x, [1, 2], 6.0, 16)):\n"
+        "    try:\n"
+        "        call()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'not built' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('returned without the library')\n"
+        "print('raised')\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root,
+                       timeout=300)
+    assert r.returncode == 0 and "raised" in r.stdout, r.stderr[-2000:]
