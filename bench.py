@@ -56,13 +56,14 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched", "serving",
-                                           "decimated"],
+                                           "decimated", "cluster"],
                     default="ska",
                     help="ska: the SKA-like FP32 chunk (default, the headline); plain: 64 x 65536 "
                          "FP32 noise + top-hats; precision: the SKA-like chunk stored as FP16 / "
                          "BF16 with Eq. 5; batched: four decimated DM ranges in one launch; "
                          "serving: 16 beams of FP16 chunks streamed with continuous batching; "
-                         "decimated: widths to 512 by decimation in time vs the plain search")
+                         "decimated: widths to 512 by decimation in time vs the plain search; "
+                         "cluster: per-DM clustering of the SKA-like chunk's candidates")
     ap.add_argument("--beams", type=int, default=16)
     ap.add_argument("--chunks-per-beam", type=int, default=3)
     ap.add_argument("--slots", type=int, default=4)
@@ -584,6 +585,38 @@ def run_other(a):
                                         "level samples (native to 512), each level its own "
                                         "MSD; f_T 7",
                             "l2": "inputs larger than L2"})
+        print(json.dumps(line))
+        return 0
+    if a.workload == "cluster":
+        n_dm, n_samp = a.n_dm, a.n_samp
+        sp = synth.ska_like(n_dm, n_samp, device=dev, seed=1611_1)   # the headline plane
+        m = spd.msd(sp.data)
+        snr, w = spd.boxcar_snr(sp.data, m, WIDTHS)
+        del sp
+        torch.cuda.empty_cache()
+        cap, gap = 1 << 24, 16
+        out = torch.empty((cap, 8), dtype=torch.int32, device=dev)
+        res = torch.zeros(16, dtype=torch.uint8, device=dev)
+        step = lambda: spd.cluster_rows(snr, w, THRESHOLD, gap, cap, out=out, result=res)
+        ms, clocks = timed(step, a.steps, a.warmup, 0)
+        cnt, st = spd.read_result(res)
+        if st != 0:
+            raise RuntimeError(f"cluster status {st}")
+        n = n_dm * n_samp
+        alg = 6 * n + 32 * min(cnt, cap)   # SNR + width read once, records written
+        ach = alg / (ms / 1e3) / 1e9
+        line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    clusters_per_step=cnt, gpu_launches=a.steps,
+                    roofline={"bound": "hbm", "kernel": "cluster_kernel", "achieved": ach,
+                              "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                              "peak_source": f"{peak_kind} hbm_gbs",
+                              "algorithmic_bytes": alg},
+                    config={"workload": f"per-DM clustering (max gap {gap} samples) of the "
+                                        f"candidates of the SKA-like {n_dm} x {n_samp} SNR "
+                                        "plane (spd_boxcar_snr: widths 1..16 + 24..256/8, "
+                                        "f_T 7)",
+                            "l2": "inputs larger than L2 (SNR + width planes %.1f GB)"
+                                  % (6 * n / 1e9)})
         print(json.dumps(line))
         return 0
     raise SystemExit(f"unknown workload {a.workload}")

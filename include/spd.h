@@ -113,6 +113,18 @@ typedef struct {
     int32_t width;
 } spd_candidate;
 
+/* One cluster of a DM row's candidates (32 bytes), from spd_cluster_rows. */
+typedef struct {
+    int32_t dm;
+    int32_t first;        /* sample of the cluster's first candidate */
+    int32_t last;         /* sample of its last candidate */
+    int32_t peak_sample;  /* sample of its highest SNR (the earliest among equals) */
+    float peak_snr;
+    int32_t peak_width;   /* the width at peak_sample */
+    int32_t members;      /* candidates in the cluster */
+    int32_t reserved0;
+} spd_cluster;
+
 /* Device-side summary written by the candidate-producing calls (16 bytes).
  * count: exact number of samples with SNR >= threshold, even when it exceeds
  * the capacity (then only `capacity` records are written, which ones is
@@ -262,6 +274,28 @@ spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int
  * SPD_ERR_CUDA. */
 spd_status spd_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, int64_t n_samp,
                                int64_t stride, float threshold, void *stream);
+
+/* An extension after step (d): per-DM clustering of the candidates in time.
+ * Sec. 2.4 leaves the list unordered and does no clustering; this groups it.
+ * A row's candidates are its samples with snr >= threshold (exactly the
+ * records of spd_threshold_candidates). Taken in sample order, a candidate
+ * joins the previous candidate's cluster when it lies at most max_gap samples
+ * after it, and otherwise starts a new cluster. Equivalently, a cluster is a
+ * connected component of the graph that links any two candidates at most
+ * max_gap samples apart. Each cluster becomes one spd_cluster record;
+ * records are appended in no particular order.
+ *   snr, width: device planes [n_dm][stride] (e.g. spd_boxcar_snr's output);
+ *     a NaN SNR is never a candidate.
+ *   max_gap: >= 1 (1 groups only adjacent samples).
+ *   out: device array of `capacity` records, 16-byte aligned (may be NULL when
+ *     capacity is 0); result_dev->count is set to the exact number of
+ *     clusters (the call zeroes it first), and only the first `capacity`
+ *     records are written.
+ * One warp scans one row.  Errors: SPD_ERR_INVALID_ARG, SPD_ERR_CUDA. */
+spd_status spd_cluster_rows(const float *snr, const uint16_t *width, int64_t n_dm,
+                            int64_t n_samp, int64_t stride, float threshold, int32_t max_gap,
+                            spd_cluster *out, int64_t capacity, spd_result *result_dev,
+                            void *stream);
 
 /* Bytes of device workspace spd_detect / spd_search need. */
 size_t spd_detect_workspace_bytes(const spd_plane *plane, const spd_search_params *params);

@@ -291,6 +291,44 @@ def threshold_plane(best, width, thr: float):
     return np.where(keep, best, 0.0), np.where(keep, np.asarray(width), 0)
 
 
+def cluster_rows(best, width, thr: float, max_gap: int, row0: int = 0):
+    """Per-DM clustering of the candidates in time -- an extension after Sec.
+    2.4, whose list is unordered and unclustered.  Per row, the candidates
+    (best >= thr) in sample order; a candidate joins the previous one's
+    cluster when it lies at most max_gap samples after it, else it opens a
+    new cluster.  Per cluster: first and last sample, the sample of the
+    highest SNR (the earliest among equals), that SNR and width, and the
+    number of members.  Returned in (dm, first) order."""
+    best = np.asarray(best, dtype=np.float64)
+    width = np.asarray(width)
+    recs = []
+    for r in range(best.shape[0]):
+        cur = None
+        for i in range(best.shape[1]):
+            v = best[r, i]
+            if not v >= thr:             # NaN is never a candidate
+                continue
+            if cur is not None and i - cur["last"] <= max_gap:
+                cur["last"] = i
+                cur["members"] += 1
+                if v > cur["peak_snr"]:
+                    cur.update(peak_sample=i, peak_snr=v, peak_width=int(width[r, i]))
+            else:
+                if cur is not None:
+                    recs.append(cur)
+                cur = dict(dm=row0 + r, first=i, last=i, peak_sample=i, peak_snr=v,
+                           peak_width=int(width[r, i]), members=1)
+        if cur is not None:
+            recs.append(cur)
+    out = np.zeros(len(recs), dtype=[("dm", np.int32), ("first", np.int32), ("last", np.int32),
+                                     ("peak_sample", np.int32), ("peak_snr", np.float64),
+                                     ("peak_width", np.int32), ("members", np.int32)])
+    for k, c in enumerate(recs):
+        for f in out.dtype.names:
+            out[k][f] = c[f]
+    return out
+
+
 # ------------------------------------------------------------ whole path
 
 def msd_and_sigma(plane, widths, sigma_mode=SIGMA_SQRTN, scope=SCOPE_GLOBAL, nmax=0):

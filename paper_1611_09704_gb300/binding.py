@@ -93,6 +93,9 @@ RESULT_BYTES = ctypes.sizeof(SpdResult)     # 16
 MSD_DTYPE = np.dtype([("mean", "<f8"), ("sd", "<f8"), ("sd_nmax", "<f8"), ("n", "<i8"),
                       ("nmax", "<i4"), ("status", "<i4")])
 CAND_DTYPE = np.dtype([("dm", "<i4"), ("sample", "<i4"), ("snr", "<f4"), ("width", "<i4")])
+CLUSTER_DTYPE = np.dtype([("dm", "<i4"), ("first", "<i4"), ("last", "<i4"),
+                          ("peak_sample", "<i4"), ("peak_snr", "<f4"), ("peak_width", "<i4"),
+                          ("members", "<i4"), ("reserved0", "<i4")])
 
 # Every symbol include/spd.h declares, for the export check.
 EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
@@ -105,7 +108,7 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
            "spd_sd_nmax_merge_partials", "spd_threshold_plane",
            "spd_search_decimated_workspace_bytes", "spd_search_decimated",
-           "spd_debug_set_copy_wait"]
+           "spd_debug_set_copy_wait", "spd_cluster_rows"]
 
 
 class SpdError(RuntimeError):
@@ -179,6 +182,8 @@ def load(path: str | None = None):
     lib.spd_search_decimated.restype = I32
     lib.spd_threshold_plane.argtypes = [P, P, I64, I64, I64, F, P]
     lib.spd_threshold_plane.restype = I32
+    lib.spd_cluster_rows.argtypes = [P, P, I64, I64, I64, F, I32, P, I64, P, P]
+    lib.spd_cluster_rows.restype = I32
     lib.spd_msd_shard_partial.argtypes = [pp, P, P, SZ, P]
     lib.spd_msd_shard_partial.restype = I32
     lib.spd_msd_merge_partials.argtypes = [P, I32, P, P]
@@ -380,6 +385,31 @@ def threshold_candidates(snr, width, threshold, capacity, *, n_samp=None, stream
                                         _ptr(result), _stream(stream)),
            "spd_threshold_candidates")
     return out, result
+
+
+def cluster_rows(snr, width, threshold, max_gap, capacity, *, n_samp=None, stream=None,
+                 out=None, result=None):
+    """spd_cluster_rows: per-DM clusters of the candidates (snr >= threshold),
+    a gap of at most max_gap samples joining neighbours; returns (records int32
+    [capacity, 8], result uint8 [16]).  Decode with clusters_to_numpy."""
+    if width.stride(0) != snr.stride(0):
+        raise ValueError("snr and width planes must share a row stride")
+    lib = load()
+    dev = snr.device
+    n_dm, n = snr.shape[0], (snr.shape[1] if n_samp is None else n_samp)
+    if out is None:
+        out = torch.empty((max(int(capacity), 1), 8), dtype=torch.int32, device=dev)
+    if result is None:
+        result = torch.empty(RESULT_BYTES, dtype=torch.uint8, device=dev)
+    _check(lib.spd_cluster_rows(_ptr(snr), _ptr(width), n_dm, n, snr.stride(0),
+                                float(threshold), int(max_gap), _ptr(out), int(capacity),
+                                _ptr(result), _stream(stream)), "spd_cluster_rows")
+    return out, result
+
+
+def clusters_to_numpy(out: torch.Tensor, count: int) -> np.ndarray:
+    n = min(int(count), out.shape[0])
+    return out[:n].detach().cpu().numpy().view(CLUSTER_DTYPE).reshape(-1)
 
 
 def threshold_plane(snr, width, threshold, *, n_samp=None, stream=None):

@@ -12,6 +12,7 @@
 using namespace spd;
 
 static_assert(sizeof(spd_msd_part) == sizeof(spd::MsdPart), "spd_msd_part layout");
+static_assert(sizeof(spd_cluster) == 32, "spd_cluster layout");
 
 namespace {
 
@@ -520,6 +521,28 @@ spd_status spd_threshold_candidates(const float *snr, const uint16_t *width, int
     if (empty) return SPD_OK;
     SPD_CK(launch_threshold(snr, width, n_dm, n_samp, stride, threshold, out, capacity,
                             result_dev, st));
+    return SPD_OK;
+}
+
+spd_status spd_cluster_rows(const float *snr, const uint16_t *width, int64_t n_dm,
+                            int64_t n_samp, int64_t stride, float threshold, int32_t max_gap,
+                            spd_cluster *out, int64_t capacity, spd_result *result_dev,
+                            void *stream) {
+    if (n_dm < 0 || n_samp < 0 || n_dm > INT32_MAX || n_samp > INT32_MAX)
+        return SPD_ERR_INVALID_ARG;
+    if (!result_dev || capacity < 0 || (capacity > 0 && !out) || !isfinite(threshold) ||
+        max_gap < 1)
+        return SPD_ERR_INVALID_ARG;
+    if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
+    const bool empty = n_dm == 0 || n_samp == 0;
+    if (!empty && (!snr || !width || stride < n_samp)) return SPD_ERR_INVALID_ARG;
+    if (!empty && (reinterpret_cast<uintptr_t>(snr) % 4 || reinterpret_cast<uintptr_t>(width) % 2))
+        return SPD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SPD_CK(cudaMemsetAsync(result_dev, 0, sizeof(spd_result), st));
+    if (empty) return SPD_OK;
+    SPD_CK(launch_cluster(snr, width, n_dm, n_samp, stride, threshold, max_gap, out, capacity,
+                          result_dev, st));
     return SPD_OK;
 }
 

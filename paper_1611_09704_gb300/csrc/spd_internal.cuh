@@ -190,6 +190,11 @@ cudaError_t launch_threshold_plane(float *snr, uint16_t *width, int64_t n_dm, in
 cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_dm,
                              int64_t n_samp, int64_t stride, float thr, spd_candidate *out,
                              int64_t capacity, spd_result *result, cudaStream_t s);
+// Per-DM clustering of the candidates of an SNR plane (one warp per row).
+cudaError_t launch_cluster(const float *snr, const uint16_t *width, int64_t n_dm,
+                           int64_t n_samp, int64_t stride, float thr, int64_t gap,
+                           spd_cluster *out, int64_t capacity, spd_result *result,
+                           cudaStream_t s);
 cudaError_t launch_boxcar_sums(const spd_plane &p, int w, float *out, int64_t out_stride,
                                cudaStream_t s);
 

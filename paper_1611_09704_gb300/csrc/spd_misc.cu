@@ -1,5 +1,5 @@
-// spd_misc.cu -- step (d) on a stored SNR plane (Sec. 2.4) and the raw boxcar
-// sums test aid.
+// spd_misc.cu -- step (d) on a stored SNR plane (Sec. 2.4), the per-DM
+// clustering of its candidates, and the raw boxcar sums test aid.
 #include "spd_internal.cuh"
 
 #include <math.h>
@@ -124,6 +124,92 @@ __global__ void boxcar_sums_kernel(const spd_plane p, int w, float *out, int64_t
         s = t;
     }
     *o = s;
+}
+
+// Per-DM clustering of the candidates (snr >= thr) in time: one warp scans
+// one row, 32 samples per step, kClusterSteps steps of loads in flight.  In
+// sample order a candidate joins the open cluster when it lies at most `gap`
+// samples after the previous candidate, else the open cluster is written and
+// a new one starts.  Every lane holds the same cluster state (the candidates
+// of a step are visited in order through the ballot mask and shuffles), so
+// lane 0 alone reserves and writes a record.
+constexpr int kClusterWarps = 8;   // rows per CTA
+constexpr int kClusterSteps = 8;   // 32-sample steps loaded at once per warp
+
+struct ClusterState {
+    int64_t first, last, peak_t, members;
+    float peak;
+    int peak_w;
+};
+
+__device__ __forceinline__ void emit_cluster(const ClusterState &c, int64_t row,
+                                             spd_cluster *out, int64_t capacity,
+                                             spd_result *result, int lane) {
+    if (lane != 0) return;
+    const unsigned long long idx =
+        atomicAdd(reinterpret_cast<unsigned long long *>(&result->count), 1ull);
+    if (idx < (unsigned long long)capacity) {
+        spd_cluster r;
+        r.dm = (int32_t)row;
+        r.first = (int32_t)c.first;
+        r.last = (int32_t)c.last;
+        r.peak_sample = (int32_t)c.peak_t;
+        r.peak_snr = c.peak;
+        r.peak_width = c.peak_w;
+        r.members = (int32_t)c.members;
+        r.reserved0 = 0;
+        out[idx] = r;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kClusterWarps) cluster_kernel(
+    const float *snr, const uint16_t *width, int64_t n_dm, int64_t n_samp, int64_t stride,
+    float thr, int64_t gap, spd_cluster *out, int64_t capacity, spd_result *result) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * kClusterWarps + (threadIdx.x >> 5);
+    if (row >= n_dm) return;   // the whole warp
+    const float *sp = snr + row * stride;
+    const uint16_t *wp = width + row * stride;
+    bool open = false;
+    ClusterState c{0, 0, 0, 0, 0.f, 0};
+    for (int64_t base = 0; base < n_samp; base += 32 * kClusterSteps) {
+        float v[kClusterSteps];
+        int w[kClusterSteps];
+#pragma unroll
+        for (int k = 0; k < kClusterSteps; ++k) {
+            const int64_t t = base + 32 * k + lane;
+            v[k] = t < n_samp ? __ldcs(sp + t) : -INFINITY;
+            w[k] = t < n_samp ? (int)__ldcs(wp + t) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kClusterSteps; ++k) {
+            unsigned m = __ballot_sync(0xffffffffu, v[k] >= thr);   // NaN: not a candidate
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const float sv = __shfl_sync(0xffffffffu, v[k], b);
+                const int sw = __shfl_sync(0xffffffffu, w[k], b);
+                const int64_t t = base + 32 * k + b;
+                if (open && t - c.last <= gap) {
+                    ++c.members;
+                    c.last = t;
+                    if (sv > c.peak) {   // strict: the earliest of equal peaks stays
+                        c.peak = sv;
+                        c.peak_t = t;
+                        c.peak_w = sw;
+                    }
+                } else {
+                    if (open) emit_cluster(c, row, out, capacity, result, lane);
+                    open = true;
+                    c.first = c.last = c.peak_t = t;
+                    c.members = 1;
+                    c.peak = sv;
+                    c.peak_w = sw;
+                }
+            }
+        }
+    }
+    if (open) emit_cluster(c, row, out, capacity, result, lane);
 }
 
 }  // namespace
@@ -255,6 +341,17 @@ cudaError_t launch_threshold(const float *snr, const uint16_t *width, int64_t n_
     if (tiles <= 0) return cudaSuccess;
     threshold_kernel<<<(unsigned)tiles, kThrThreads, 0, s>>>(snr, width, n_samp, stride, tpr,
                                                              thr, out, capacity, result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster(const float *snr, const uint16_t *width, int64_t n_dm,
+                           int64_t n_samp, int64_t stride, float thr, int64_t gap,
+                           spd_cluster *out, int64_t capacity, spd_result *result,
+                           cudaStream_t s) {
+    const int64_t blocks = (n_dm + kClusterWarps - 1) / kClusterWarps;
+    if (blocks <= 0 || n_samp <= 0) return cudaSuccess;
+    cluster_kernel<<<(unsigned)blocks, 32 * kClusterWarps, 0, s>>>(
+        snr, width, n_dm, n_samp, stride, thr, gap, out, capacity, result);
     return cudaGetLastError();
 }
 

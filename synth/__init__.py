@@ -209,6 +209,24 @@ def quantise_rows(sp: SynthPlane, dtype: str, q_max: float = 16384.0) -> SynthPl
                       seed=sp.seed, recipe=sp.recipe + f"; stored {dtype} with per-row scale")
 
 
+def snr_plane(n_dm, n_samp, *, stride=None, device="cpu", seed=0, levels=10, nan_frac=0.01,
+              max_width=512):
+    """A seeded stand-in for a per-sample best-SNR plane and its width plane:
+    SNRs drawn from the integers 0..levels-1 (exact in FP32, so equal peaks
+    occur), a nan_frac of them NaN, widths uniform in 1..max_width (int16
+    holding uint16).  Columns >= n_samp of a wider stride are NaN / 0."""
+    stride = n_samp if stride is None else stride
+    g = _gen(device, seed)
+    snr = torch.full((n_dm, stride), float("nan"), dtype=torch.float32, device=device)
+    v = torch.randint(0, levels, (n_dm, n_samp), generator=g, device=device).to(torch.float32)
+    nan = torch.rand((n_dm, n_samp), generator=g, device=device) < nan_frac
+    snr[:, :n_samp] = torch.where(nan, torch.full_like(v, float("nan")), v)
+    width = torch.zeros((n_dm, stride), dtype=torch.int16, device=device)
+    width[:, :n_samp] = torch.randint(1, max_width + 1, (n_dm, n_samp), generator=g,
+                                      device=device).to(torch.int16)
+    return snr, width
+
+
 def to_host_numpy(t: torch.Tensor) -> np.ndarray:
     """Host copy for the oracle: float32 as is, fp16/bf16 as raw uint16 bits."""
     t = t.detach().cpu().contiguous()

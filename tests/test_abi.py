@@ -46,6 +46,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(b.SpdResult) == 16
     assert ctypes.sizeof(b.SpdPlane) == 56
     assert b.MSD_DTYPE.itemsize == 40 and b.CAND_DTYPE.itemsize == 16
+    assert b.CLUSTER_DTYPE.itemsize == 32
 
 
 def test_ctypes_layouts_match_the_c_compiler(tmp_path):
@@ -64,6 +65,13 @@ def test_ctypes_layouts_match_the_c_compiler(tmp_path):
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in ct._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    # the numpy record dtypes the binding decodes device arrays with
+    dtypes = {"spd_candidate": b.CAND_DTYPE, "spd_cluster": b.CLUSTER_DTYPE,
+              "spd_msd_stats": b.MSD_DTYPE}
+    for cname, dt in dtypes.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in dt.names:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
     lines += ["return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -79,6 +87,10 @@ def test_ctypes_layouts_match_the_c_compiler(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(ct), cname
         for f, _ in ct._fields_:
             assert got[(cname, f)] == getattr(ct, f).offset, (cname, f)
+    for cname, dt in dtypes.items():
+        assert got[(cname, "size")] == dt.itemsize, cname
+        for f in dt.names:
+            assert got[(cname, f)] == dt.fields[f][1], (cname, f)
 
 
 def test_stream_host_validation(lib):

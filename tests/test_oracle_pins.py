@@ -425,6 +425,70 @@ def test_search_end_to_end_against_brute_force(seed):
     assert np.array_equal(cands["width"], want_w[want_b >= thr])
 
 
+def _components(best, width, thr, gap):
+    """Clusters as connected components of the graph that links any two
+    candidates of a row at most `gap` samples apart (union-find over every
+    pair): a statement independent of the oracle's sequential scan."""
+    out = []
+    for r in range(best.shape[0]):
+        idx = [i for i in range(best.shape[1]) if best[r, i] >= thr]
+        parent = {i: i for i in idx}
+
+        def find(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+        for a in idx:
+            for b in idx:
+                if a < b and b - a <= gap:
+                    parent[find(b)] = find(a)
+        comps = {}
+        for i in idx:
+            comps.setdefault(find(i), []).append(i)
+        for m in comps.values():
+            vals = [best[r, i] for i in m]
+            k = int(np.argmax(vals))           # the first of equal maxima
+            out.append((r, m[0], m[-1], m[k], vals[k], int(width[r, m[k]]), len(m)))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cluster_rows_against_components(seed):
+    rng = np.random.default_rng(900 + seed)
+    n_dm, n = int(rng.integers(1, 4)), int(rng.integers(1, 90))
+    best = rng.integers(0, 10, size=(n_dm, n)).astype(np.float64)
+    best[rng.random((n_dm, n)) < 0.05] = np.nan
+    width = rng.integers(1, 300, size=(n_dm, n))
+    thr, gap = float(rng.integers(4, 9)), int(rng.integers(1, 6))
+    c = oracle.cluster_rows(best, width, thr, gap)
+    got = sorted((int(x["dm"]), int(x["first"]), int(x["last"]), int(x["peak_sample"]),
+                  float(x["peak_snr"]), int(x["peak_width"]), int(x["members"])) for x in c)
+    assert got == _components(best, width, thr, gap)
+    # the members are exactly the candidates
+    assert int(c["members"].sum()) == int(np.sum(best >= thr))
+
+
+def test_cluster_rows_closed_forms():
+    """Isolated spikes further apart than the gap: one cluster each; a
+    contiguous run: one cluster spanning it, peaked at its first maximum; a
+    gap of exactly max_gap joins, max_gap + 1 splits; row0 offsets dm."""
+    best = np.zeros((2, 40))
+    best[0, [3, 10, 20]] = 7.0
+    best[1, 5:12] = [6, 8, 9, 9, 7, 6, 6]
+    w = np.arange(80).reshape(2, 40)
+    c = oracle.cluster_rows(best, w, 6.0, 4, row0=100)
+    assert list(c["dm"]) == [100, 100, 100, 101]
+    assert list(c["first"]) == [3, 10, 20, 5] and list(c["last"]) == [3, 10, 20, 11]
+    assert list(c["members"]) == [1, 1, 1, 7]
+    assert c["peak_sample"][3] == 7 and c["peak_snr"][3] == 9 and c["peak_width"][3] == 47
+    x = np.zeros((1, 20))
+    x[0, [2, 5, 9]] = 8.0                       # gaps of 3 and 4
+    assert len(oracle.cluster_rows(x, np.ones((1, 20)), 8.0, 3)) == 2
+    assert len(oracle.cluster_rows(x, np.ones((1, 20)), 8.0, 4)) == 1
+    assert len(oracle.cluster_rows(np.full((1, 5), np.nan), np.ones((1, 5)), 0.0, 1)) == 0
+
+
 def test_snr_at_matches_closed_form():
     """One-pair SNR: a ramp's window sum is closed-form; past the row end NaN."""
     n, a, b = 50, 2.0, 0.5
