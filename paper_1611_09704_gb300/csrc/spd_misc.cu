@@ -130,17 +130,28 @@ __global__ void boxcar_sums_kernel(const spd_plane p, int w, float *out, int64_t
 // one row, 32 samples per step, kClusterSteps steps of loads in flight.  In
 // sample order a candidate joins the open cluster when it lies at most `gap`
 // samples after the previous candidate, else the open cluster is written and
-// a new one starts.  Every lane holds the same cluster state (the candidates
-// of a step are visited in order through the ballot mask and shuffles), so
-// lane 0 alone reserves and writes a record.
+// a new one starts.  A step is taken a segment at a time, not a candidate at a
+// time: each lane finds its previous candidate (in the step's ballot mask, or
+// the open cluster's last), the lanes that start a cluster form a second mask,
+// and each segment between starts is absorbed with a popcount, its highest
+// set bit, and one warp max (redux) over order-preserving keys of its SNRs.
+// Every lane holds the same cluster state, so lane 0 alone writes records.
 constexpr int kClusterWarps = 8;   // rows per CTA
 constexpr int kClusterSteps = 8;   // 32-sample steps loaded at once per warp
 
 struct ClusterState {
     int64_t first, last, peak_t, members;
     float peak;
+    unsigned peak_key;
     int peak_w;
 };
+
+// Monotone map of a non-NaN float to an unsigned key (larger float, larger
+// key); every key is > 0, so 0 stands for "no member".
+__device__ __forceinline__ unsigned order_key(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
 
 __device__ __forceinline__ void emit_cluster(const ClusterState &c, int64_t row,
                                              spd_cluster *out, int64_t capacity,
@@ -162,6 +173,24 @@ __device__ __forceinline__ void emit_cluster(const ClusterState &c, int64_t row,
     }
 }
 
+// The members M (a lane mask of this step, starting at sample t0) join the
+// open cluster: count, last sample, and the peak (strict: an earlier equal
+// peak stays; within M the lowest lane of the maximum).
+__device__ __forceinline__ void absorb(ClusterState &c, unsigned M, int64_t t0, unsigned key,
+                                       float v, int w, int lane) {
+    c.members += __popc(M);
+    c.last = t0 + (31 - __clz(M));
+    const unsigned mine = ((M >> lane) & 1u) ? key : 0u;
+    const unsigned kmax = __reduce_max_sync(0xffffffffu, mine);
+    if (kmax > c.peak_key) {
+        const int pl = __ffs(__ballot_sync(0xffffffffu, mine == kmax)) - 1;
+        c.peak_key = kmax;
+        c.peak = __shfl_sync(0xffffffffu, v, pl);
+        c.peak_w = __shfl_sync(0xffffffffu, w, pl);
+        c.peak_t = t0 + pl;
+    }
+}
+
 __global__ void __launch_bounds__(32 * kClusterWarps) cluster_kernel(
     const float *snr, const uint16_t *width, int64_t n_dm, int64_t n_samp, int64_t stride,
     float thr, int64_t gap, spd_cluster *out, int64_t capacity, spd_result *result) {
@@ -171,7 +200,7 @@ __global__ void __launch_bounds__(32 * kClusterWarps) cluster_kernel(
     const float *sp = snr + row * stride;
     const uint16_t *wp = width + row * stride;
     bool open = false;
-    ClusterState c{0, 0, 0, 0, 0.f, 0};
+    ClusterState c{0, 0, 0, 0, 0.f, 0u, 0};
     for (int64_t base = 0; base < n_samp; base += 32 * kClusterSteps) {
         float v[kClusterSteps];
         int w[kClusterSteps];
@@ -183,29 +212,32 @@ __global__ void __launch_bounds__(32 * kClusterWarps) cluster_kernel(
         }
 #pragma unroll
         for (int k = 0; k < kClusterSteps; ++k) {
-            unsigned m = __ballot_sync(0xffffffffu, v[k] >= thr);   // NaN: not a candidate
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const float sv = __shfl_sync(0xffffffffu, v[k], b);
-                const int sw = __shfl_sync(0xffffffffu, w[k], b);
-                const int64_t t = base + 32 * k + b;
-                if (open && t - c.last <= gap) {
-                    ++c.members;
-                    c.last = t;
-                    if (sv > c.peak) {   // strict: the earliest of equal peaks stays
-                        c.peak = sv;
-                        c.peak_t = t;
-                        c.peak_w = sw;
-                    }
-                } else {
-                    if (open) emit_cluster(c, row, out, capacity, result, lane);
-                    open = true;
-                    c.first = c.last = c.peak_t = t;
-                    c.members = 1;
-                    c.peak = sv;
-                    c.peak_w = sw;
-                }
+            const bool cand = v[k] >= thr;   // NaN: not a candidate
+            const unsigned m = __ballot_sync(0xffffffffu, cand);
+            if (!m) continue;
+            const int64_t t0 = base + 32 * k;
+            // does this lane's candidate start a cluster?
+            const unsigned below = m & ((1u << lane) - 1u);
+            const bool has_prev = below != 0u || open;
+            const int64_t prev = below ? t0 + (31 - __clz(below)) : c.last;
+            const bool start = cand && (!has_prev || (t0 + lane) - prev > gap);
+            unsigned S = __ballot_sync(0xffffffffu, start);
+            const unsigned key = cand ? order_key(v[k]) : 0u;
+            // members before the first start continue the open cluster
+            const int fs = S ? __ffs(S) - 1 : 32;
+            const unsigned cont = fs == 32 ? m : (m & ((1u << fs) - 1u));
+            if (cont) absorb(c, cont, t0, key, v[k], w[k], lane);
+            while (S) {
+                const int s0 = __ffs(S) - 1;
+                S &= S - 1u;
+                const int e = S ? __ffs(S) - 1 : 32;
+                const unsigned seg = m & (0xffffffffu << s0) & (e == 32 ? 0xffffffffu : ((1u << e) - 1u));
+                if (open) emit_cluster(c, row, out, capacity, result, lane);
+                open = true;
+                c.first = t0 + s0;
+                c.members = 0;
+                c.peak_key = 0u;
+                absorb(c, seg, t0, key, v[k], w[k], lane);
             }
         }
     }
