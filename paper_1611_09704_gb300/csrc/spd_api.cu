@@ -91,10 +91,14 @@ MsdLayout msd_layout(const spd_plane *p, int nmax = 0) {
 // by the listed widths.  They are cut into groups of consecutive widths that
 // step by 1 (the running sum adds one sample per width) or by G (it adds one
 // G-sample window sum); a group's sums start from the block sums at `off`.
-// Groups hold at most 16 (step 1) or 4 (16/G + 1) (step G) widths times
-// `scale`, doubled until there are at most 64 groups, and never cross a
-// multiple of 64 in eval index.  G is the most frequent step of 8 or 16, if any.
-spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, int scale0 = 1) {
+// Groups hold at most 16 (step 1) widths times `scale`, and at most
+// 4 (16/G + 1) (step G; plane output) or 4 (candidate search, where each group
+// has its own bound) widths times `scale`; `scale` doubles until there are at
+// most 64 groups, and groups never cross a multiple of 64 in eval index.  G is
+// the most frequent step of 8 or 16, if any.  In the candidate search the
+// group of widths 1..16 is marked for the per-sample energy test.
+spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, int scale0 = 1,
+                           bool search = false) {
     if (!widths || n < 1 || n > SPD_MAX_WIDTHS) return SPD_ERR_INVALID_ARG;
     for (int k = 0; k < n; ++k) {
         if (widths[k] < 1 || widths[k] > SPD_MAX_WIDTH) return SPD_ERR_INVALID_ARG;
@@ -116,7 +120,8 @@ spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, in
     for (int scale = scale0 < 1 ? 1 : scale0;; scale *= 2) {
         // coarse groups hold 4 (16 / G + 1) widths at scale 1: their start and
         // merge cost more than a fine group's relative to their widths
-        const int max_fine = 16 * scale, max_coarse = (G ? 4 * (16 / G + 1) : 1) * scale;
+        const int max_fine = 16 * scale;
+        const int max_coarse = (G ? (search ? 4 : 4 * (16 / G + 1)) : 1) * scale;
         groups.clear();
         for (int k = 0; k < ne; ++k) {
             const int step = k ? E[k] - E[k - 1] : 1;
@@ -147,8 +152,25 @@ spd_status compile_program(const int32_t *widths, int32_t n, RangeProg &prog, in
     prog.n_eval = ne;
     prog.wmax = E.back();
     prog.G = G;
-    for (size_t i = 0; i < groups.size(); ++i) prog.groups[i] = groups[i];
+    for (size_t i = 0; i < groups.size(); ++i) {
+        Group g = groups[i];
+        if (search && !(g.flags & kGroupCoarse) && g.off == 0 && g.count == 16)
+            g.flags |= kGroupRefine;
+        prog.groups[i] = g;
+    }
     return SPD_OK;
+}
+
+// Highest block max table level any group of a program reads (0: none).
+int prog_kmax(const RangeProg &prog) {
+    int k = 0;
+    for (int i = 0; i < prog.n_groups; ++i) {
+        const Group &g = prog.groups[i];
+        const int d = (g.flags & kGroupCoarse) ? prog.G : 1;
+        const GroupGeom q = group_geom(g.off, g.count, d);
+        if (q.lvl > k) k = q.lvl;
+    }
+    return k;
 }
 
 // Blocks of 16 positions staged per tile: the tile, the halo and slack for
@@ -284,9 +306,22 @@ spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out,
     L.out_stride = out_stride;
     L.wait_ns = g_wait_ns;
     L.extra_tx = g_extra_tx;
-    const size_t smem = launch_smem(R, raw, max_eval, G);
+    if (snr_out) {   // plane output: every sample's best SNR and width
+        const size_t smem = launch_smem(R, raw, max_eval, G);
+        if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
+        SPD_CK(launch_detect(L, dtype, G, true, max_eval > 64, smem, ctas_per_sm, st));
+        return SPD_OK;
+    }
+    int kmax = 0;
+    for (int i = 0; i < n; ++i) {
+        const int k = prog_kmax(rd[i].prog);
+        kmax = k > kmax ? k : kmax;
+    }
+    L.R = (R + 3) & ~3;
+    L.kmax = kmax;
+    const size_t smem = search_smem_bytes(L.R, raw, max_eval, kmax, G);
     if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
-    SPD_CK(launch_detect(L, dtype, G, snr_out != nullptr, max_eval > 64, smem, ctas_per_sm, st));
+    SPD_CK(launch_search(L, dtype, G, max_eval > 64, smem, ctas_per_sm, st));
     return SPD_OK;
 }
 
@@ -560,7 +595,7 @@ spd_status spd_detect(const spd_plane *plane, const spd_search_params *params,
     SPD_TRY(check_plane(plane));
     SPD_TRY(check_params(params));
     static thread_local RangeProg prog;
-    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog, 1, true));
     if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
     if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -593,7 +628,7 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
     SPD_TRY(check_plane(plane));
     SPD_TRY(check_params(params));
     static thread_local RangeProg prog;
-    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog, 1, true));
     if (!result_dev || capacity < 0 || (capacity > 0 && !out)) return SPD_ERR_INVALID_ARG;
     if (out && reinterpret_cast<uintptr_t>(out) % 16) return SPD_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -635,7 +670,7 @@ spd_status batch_plan(const spd_range *ranges, int n, const spd_tuning *tuning,
         SPD_TRY(check_plane(&r.plane));
         SPD_TRY(check_params(&r.params));
         if (r.dm_offset < 0 || r.decimation < 0) return SPD_ERR_INVALID_ARG;
-        SPD_TRY(compile_program(r.params.widths, r.params.n_widths, progs[i], scale));
+        SPD_TRY(compile_program(r.params.widths, r.params.n_widths, progs[i], scale, true));
         const int64_t entries = entries_of(&r.plane, r.params.msd_scope);
         L.msd_off[i] = off;
         L.msd_bytes[i] = msd_layout(&r.plane, nmax_of(&r.params)).total;
@@ -869,7 +904,7 @@ spd_status stream_layout(int64_t n_dm, int32_t dtype, const spd_search_params *p
         return SPD_ERR_INVALID_ARG;
     SPD_TRY(check_params(params));
     if (params->sigma_mode != SPD_SIGMA_SQRTN) return SPD_ERR_UNSUPPORTED;
-    SPD_TRY(compile_program(params->widths, params->n_widths, prog));
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog, 1, true));
     L.entries = params->msd_scope == SPD_MSD_PER_ROW ? n_dm : 1;
     L.halo_cap = ((prog.wmax - 1) + 7) / 8 * 8;
     L.msd_off = 0;

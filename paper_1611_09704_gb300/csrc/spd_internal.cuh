@@ -88,6 +88,7 @@ struct Group {
     uint16_t flags;   // bit 0: step G (window sums), else step 1
 };
 constexpr uint16_t kGroupCoarse = 1;
+constexpr uint16_t kGroupRefine = 2;   // widths 1..16 from off 0: per-sample energy test first
 
 constexpr int kMaxCodeGroups = 64;          // groups a packed max can tell apart
 constexpr int kMaxEval = SPD_MAX_WIDTHS + 1;
@@ -144,9 +145,78 @@ struct Launch {
     int64_t out_stride;
     uint64_t wait_ns;           // bound of a wait for a bulk copy
     uint32_t extra_tx;          // test aid: bytes expected beyond each copy (0 in use)
-    uint32_t reserved0;
+    int32_t kmax;               // search kernel: levels of the block max table
     RangeDesc rng[kMaxRanges];
 };
+
+// ------------------------------------------------------------ search kernel
+
+constexpr int kSPad = 20;          // shared words per 16 positions (4 padding words)
+constexpr int kSLevels = 5;        // block max table: windows of up to 2^5 blocks
+
+// Bound geometry of one width group (Group) of step d, for the unit of 16
+// starts 16t .. 16t+15: its windows end in blocks t + a .. t + b and lie in
+// blocks t .. t + e - 1.  The largest block prefix over [t + a, t + b] is
+// read as the max of two table windows of 2^lvl blocks at t + a and t + bk
+// (lvl = -1: a plain loop over the blocks, for spans longer than the table).
+struct GroupGeom {
+    int a, bk, lvl, e;
+};
+__host__ __device__ inline GroupGeom group_geom(int off, int count, int d) {
+    GroupGeom q;
+    q.a = (off + d) >> 4;
+    const int b = (15 + off + count * d) >> 4;
+    const int len = b - q.a + 1;
+    q.lvl = -1;
+    q.bk = b;
+    if (len <= (2 << kSLevels)) {
+        int k = 0;
+        while ((2 << k) <= len) ++k;   // floor(log2(len))
+        if (k > kSLevels) k = kSLevels;
+        q.lvl = k;
+        q.bk = b - (1 << k) + 1;
+    }
+    q.e = 1 + ((14 + off + count * d) >> 4);
+    return q;
+}
+
+// Shared memory of one search CTA, in the order the kernel lays it out:
+// mbarrier (16 B), one raw staging buffer, then FP32 arrays -- centred samples
+// y, in-block prefix sums P and (G > 1) G-sample window sums, each 20 words
+// per 16 positions; per block: sums, prefix maxima (level 0 of the table) and
+// kmax table levels, prefix minima, energy prefix (RM + 4), four scan
+// temporaries; 1/sigma_w per eval index -- then per group two int4 of
+// evaluation and bound data, and the width per eval index (uint16).
+// RM is a multiple of 4.
+struct SearchSmem {
+    size_t raw, y, p, g, bs, mx, mn, pq, ex, eq, rh, rl, inv, gr, ew, total;
+};
+__host__ __device__ inline SearchSmem search_smem(int RM, int raw_bytes, int max_eval, int kmax,
+                                                  int G) {
+    SearchSmem m;
+    const size_t blk = (size_t)kSPad * RM * sizeof(float);
+    const size_t arr = (size_t)RM * sizeof(float);
+    m.raw = 16;
+    m.y = m.raw + (size_t)raw_bytes;
+    m.p = m.y + blk;
+    m.g = m.p + blk;
+    m.bs = m.g + (G > 1 ? blk : 0);
+    m.mx = m.bs + arr;                       // level 0; levels 1..kmax follow
+    m.mn = m.mx + (size_t)(1 + kmax) * arr;
+    m.pq = m.mn + arr;
+    m.ex = m.pq + arr + 16;
+    m.eq = m.ex + arr;
+    m.rh = m.eq + arr;
+    m.rl = m.rh + arr;
+    m.inv = m.rl + arr;
+    m.gr = m.inv + (((size_t)max_eval * sizeof(float) + 15) & ~(size_t)15);
+    m.ew = m.gr + (size_t)kMaxCodeGroups * 32;
+    m.total = (m.ew + (size_t)max_eval * sizeof(uint16_t) + 15) & ~(size_t)15;
+    return m;
+}
+inline size_t search_smem_bytes(int RM, int raw_bytes, int max_eval, int kmax, int G) {
+    return search_smem(RM, raw_bytes, max_eval, kmax, G).total;
+}
 
 struct ConstArgs {
     const spd_msd_stats *msd;   // [entries]
@@ -182,6 +252,9 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
                         spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
                           size_t smem, int ctas_per_sm, cudaStream_t s);
+// The candidate search (search kernel): same launch description, kmax set.
+cudaError_t launch_search(const Launch &L, int dtype, int G, bool multi_block, size_t smem,
+                          int ctas_per_sm, cudaStream_t s);
 // x[2j] + x[2j+1] of a plane (dequantised) into an FP32 plane, j < n_out.
 cudaError_t launch_decimate2(const spd_plane &p, float *dst, int64_t n_out, int64_t dst_stride,
                              cudaStream_t s);

@@ -1,0 +1,7 @@
+// spd_search_f32.cu -- candidate search kernels for f32 planes (one translation
+// unit per storage type so that the instantiations compile in parallel).
+#include "spd_search_kernel.cuh"
+
+namespace spd {
+template cudaError_t launch_search_dt<SPD_F32>(const Launch &, int, bool, size_t, int, cudaStream_t);
+}  // namespace spd
