@@ -333,15 +333,18 @@ typedef struct {
     int32_t decimation;
 } spd_range;
 
-/* Launch shape of the detect kernel (what the autotuner chooses).
+/* Launch shape of the candidate search kernel (what the autotuner chooses).
  * ctas_per_sm: persistent CTAs per SM, 0 = as many as fit.
- * group_scale: widths per group are 16 (step 1) or 4 (16/G + 1) (step G)
- *   times this factor (>= 1): larger groups mean fewer bounds and group starts,
- *   smaller groups a finer pruning of the candidate search. */
+ * group_scale: widths per group are 16 (step 1) or 4 (step G) times this
+ *   factor (>= 1): larger groups mean fewer bounds and group starts, smaller
+ *   groups a finer pruning.
+ * tile_threads: threads per CTA, 128 or 256 (0 = 256); a CTA searches tiles
+ *   of 16 * tile_threads consecutive starts of a row, each staged once with
+ *   its (wmax - 1)-sample halo.  Other values: SPD_ERR_INVALID_ARG. */
 typedef struct {
     int32_t ctas_per_sm;
     int32_t group_scale;
-    int32_t reserved0;
+    int32_t tile_threads;
     int32_t reserved1;
 } spd_tuning;
 

@@ -64,7 +64,7 @@ class SpdRange(ctypes.Structure):
 
 class SpdTuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("group_scale", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("tile_threads", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class SpdStreamInfo(ctypes.Structure):
@@ -537,7 +537,8 @@ def _tuning(t):
         return None
     if isinstance(t, SpdTuning):
         return t
-    return SpdTuning(int(t.get("ctas_per_sm", 0)), int(t.get("group_scale", 1)), 0, 0)
+    return SpdTuning(int(t.get("ctas_per_sm", 0)), int(t.get("group_scale", 1)),
+                     int(t.get("tile_threads", 0)), 0)
 
 
 def search_batched_workspace_bytes(specs, tuning=None) -> int:

@@ -277,19 +277,41 @@ thread_local uint64_t g_wait_ns = 2000000000ull;
 thread_local uint32_t g_extra_tx = 0;
 
 // One detect launch over ranges rd[0 .. n) (same storage type and G).
+// The candidate search takes tiles of 16 * threads starts (threads 128 or
+// 256; 0 = the default); the plane output tiles of kTile.
 spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out, int64_t cap,
                       spd_result *result, float *snr_out, uint16_t *width_out,
-                      int64_t out_stride, int ctas_per_sm, cudaStream_t st) {
+                      int64_t out_stride, int ctas_per_sm, cudaStream_t st, int threads = 0) {
     static thread_local Launch L;
     memset(&L, 0, sizeof(L));
+    const int nt = (threads == 128 || threads == 256) ? threads : kSearchThreads;
+    // candidate search: U units of 16 starts per tile, the threads less the
+    // widest range's halo blocks when that leaves one block per thread
+    int halo = 0;
+    for (int i = 0; i < n; ++i) {
+        const int h = (rd[i].prog.wmax + 32 + 15) / 16 + 1;
+        halo = h > halo ? h : halo;
+    }
+    const int units = halo <= 64 ? nt - halo : nt;
     int64_t tiles = 0;
     int R = 0, raw = 0, max_eval = 0, G = rd[0].prog.G;
     for (int i = 0; i < n; ++i) {
         L.rng[i] = rd[i];
+        if (!snr_out) {
+            const int tile = kX * units;
+            L.rng[i].tiles_per_row = (rd[i].n_samp + tile - 1) / tile;
+            L.rng[i].R = (tile + rd[i].prog.wmax + 32 + 15) / 16 + 1;
+            // the window rounded up to whole 16-byte pieces: one bulk copy
+            // brings all of it (a tail fetched by plain loads would put a
+            // global-memory latency into every tile's staging); the extra
+            // samples lie in no evaluated window
+            const int per16 = 16 / (int)elem_bytes(dtype);
+            L.rng[i].span = (tile + rd[i].prog.wmax - 1 + per16 - 1) / per16 * per16;
+        }
         L.rng[i].tile0 = tiles;
-        tiles += rd[i].n_dm * rd[i].tiles_per_row;
-        R = rd[i].R > R ? rd[i].R : R;
-        const int rb = raw_bytes_of(rd[i].span, dtype);
+        tiles += L.rng[i].n_dm * L.rng[i].tiles_per_row;
+        R = L.rng[i].R > R ? L.rng[i].R : R;
+        const int rb = raw_bytes_of(L.rng[i].span, dtype);
         raw = rb > raw ? rb : raw;
         max_eval = rd[i].prog.n_eval > max_eval ? rd[i].prog.n_eval : max_eval;
     }
@@ -319,9 +341,10 @@ spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out,
     }
     L.R = (R + 3) & ~3;
     L.kmax = kmax;
+    L.units = units;
     const size_t smem = search_smem_bytes(L.R, raw, max_eval, kmax, G);
     if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
-    SPD_CK(launch_search(L, dtype, G, max_eval > 64, smem, ctas_per_sm, st));
+    SPD_CK(launch_search(L, dtype, G, max_eval > 64, smem, ctas_per_sm, nt, st));
     return SPD_OK;
 }
 
@@ -664,6 +687,9 @@ spd_status batch_plan(const spd_range *ranges, int n, const spd_tuning *tuning,
     if (!ranges || n < 1 || n > kMaxRanges) return SPD_ERR_INVALID_ARG;
     const int scale = tuning && tuning->group_scale > 0 ? tuning->group_scale : 1;
     if (tuning && (tuning->ctas_per_sm < 0 || tuning->group_scale < 0)) return SPD_ERR_INVALID_ARG;
+    if (tuning && tuning->tile_threads != 0 && tuning->tile_threads != 128 &&
+        tuning->tile_threads != 256)
+        return SPD_ERR_INVALID_ARG;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         const spd_range &r = ranges[i];
@@ -768,7 +794,8 @@ spd_status batched_impl(const spd_range *ranges, int32_t n_ranges, const spd_tun
             done[j] = true;
         }
         SPD_TRY(run_launch(grp, m, ranges[i].plane.dtype, out, capacity, result_dev, nullptr,
-                           nullptr, 0, tuning ? tuning->ctas_per_sm : 0, st));
+                           nullptr, 0, tuning ? tuning->ctas_per_sm : 0, st,
+                           tuning ? tuning->tile_threads : 0));
     }
     return SPD_OK;
 }

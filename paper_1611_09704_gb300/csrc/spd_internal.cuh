@@ -146,6 +146,8 @@ struct Launch {
     uint64_t wait_ns;           // bound of a wait for a bulk copy
     uint32_t extra_tx;          // test aid: bytes expected beyond each copy (0 in use)
     int32_t kmax;               // search kernel: levels of the block max table
+    int32_t units;              // search kernel: units of 16 starts per tile (<= threads)
+    int32_t reserved1;
     RangeDesc rng[kMaxRanges];
 };
 
@@ -252,9 +254,11 @@ cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_sc
                         spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
                           size_t smem, int ctas_per_sm, cudaStream_t s);
-// The candidate search (search kernel): same launch description, kmax set.
+// The candidate search (search kernel): same launch description with the
+// ranges' tiles of 16 * threads starts (threads = 128 or 256), kmax set.
 cudaError_t launch_search(const Launch &L, int dtype, int G, bool multi_block, size_t smem,
-                          int ctas_per_sm, cudaStream_t s);
+                          int ctas_per_sm, int threads, cudaStream_t s);
+constexpr int kSearchThreads = 256;   // threads of a search CTA by default
 // x[2j] + x[2j+1] of a plane (dequantised) into an FP32 plane, j < n_out.
 cudaError_t launch_decimate2(const spd_plane &p, float *dst, int64_t n_out, int64_t dst_stride,
                              cudaStream_t s);

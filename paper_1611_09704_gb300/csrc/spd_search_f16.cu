@@ -3,5 +3,6 @@
 #include "spd_search_kernel.cuh"
 
 namespace spd {
-template cudaError_t launch_search_dt<SPD_F16>(const Launch &, int, bool, size_t, int, cudaStream_t);
+template cudaError_t launch_search_dt<SPD_F16>(const Launch &, int, bool, size_t, int, int,
+                                                  cudaStream_t);
 }  // namespace spd

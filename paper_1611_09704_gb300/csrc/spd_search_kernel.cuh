@@ -3,8 +3,11 @@
 // thresholding with compaction; Sec. 2.3-2.4, Algorithm 1) over one or more
 // DM ranges in one persistent launch.
 //
-// CTAs of 256 threads walk tiles of 4096 consecutive start samples of one DM
-// row.  A tile's window (the tile plus the (wmax - 1)-sample halo) arrives in
+// CTAs of 256 (or 128) threads walk tiles of 16 U consecutive start samples
+// of one DM row, U = the threads less the halo's blocks, so that every thread
+// stages one block of the window (U = the threads for halos of more than 64
+// blocks, staged in several rounds).  A tile's window (the tile plus the
+// (wmax - 1)-sample halo) arrives in
 // shared memory by one 1-D bulk (TMA) copy, issued for the next tile as soon
 // as the current one has been staged, so it overlaps the whole search of the
 // current tile.
@@ -343,10 +346,10 @@ __device__ __forceinline__ void start_generic(float (&v)[kX], const float *s_y, 
 __device__ __forceinline__ void load_search_consts(const RangeDesc &rd, int entry, int RM,
                                                    float *s_inv, int4 *s_gr, uint16_t *s_ew) {
     const RangeProg &rp = rd.prog;
-    for (int q = threadIdx.x; q < rp.n_eval; q += kThreads)
+    for (int q = threadIdx.x; q < rp.n_eval; q += blockDim.x)
         s_inv[q] = rd.inv_tab[(int64_t)entry * rp.n_eval + q];
     __syncthreads();
-    for (int gi = threadIdx.x; gi < rp.n_groups; gi += kThreads) {
+    for (int gi = threadIdx.x; gi < rp.n_groups; gi += blockDim.x) {
         const Group g = rp.groups[gi];
         const int d = (g.flags & kGroupCoarse) ? rp.G : 1;
         float imax = 0.f, m2 = 0.f;
@@ -386,8 +389,13 @@ struct TilePos {
     int64_t row, col;
 };
 
-template <int DT, int G, bool MG>
-__global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_constant__ Launch L) {
+template <int DT, int G, bool MG, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_constant__ Launch L) {
+    constexpr int kThreads = NT;
+    // units of 16 starts per tile: NT less the halo blocks when the whole
+    // window then fits one block per thread (one staging round), else NT
+    const int U = L.units;
+    const int64_t kTile = (int64_t)kX * U;   // starts of one tile
     using T = typename Elem<DT>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int RM = L.R;          // multiple of 4
@@ -469,6 +477,54 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
     int64_t key = -1;                       // (range, scope entry) of the constants loaded
     int64_t skey = -1;                      // (range, row) whose scale and offset are held
     float sc = 1.f, of = 0.f;
+    // The candidates of a tile are written during the next tile: its first
+    // barrier publishes the warps' counts, one thread reserves the tile's
+    // slice of the list while the others stage, and after the staging barrier
+    // each warp writes its records.  Until then they wait in registers: SNR
+    // bits, widths (two per word), sample and row fields.
+    constexpr int kAtomicThread = kThreads - 32;   // lane 0 of the last warp
+    uint32_t pmask = 0, pbits[kX], pobk[MG ? kX / 4 : 1];
+    int pdm = 0, psb = 0, psh = 0, pwtot = 0;
+    auto reserve = [&]() {   // kAtomicThread: slices of the last tile's records
+        int tot = 0, pre[kThreads / 32];
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            pre[w] = tot;
+            tot += s_wsum[w];
+        }
+        unsigned long long base = 0;
+        if (tot)
+            base = atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
+                             (unsigned long long)tot);
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) s_wbase[w] = base + (unsigned long long)pre[w];
+    };
+    auto flush = [&]() {     // a warp writes the last tile's records
+        if (!pwtot) return;   // warp-uniform
+        // records start index by start index: for start q the lanes holding a
+        // candidate there write consecutive slots (rank among them by
+        // ballot), so each store instruction is one coalesced run
+        const unsigned long long wb = s_wbase[warp];
+        const long long room = (long long)L.capacity - (long long)wb;
+        const int nroom = room <= 0 ? 0 : (room < pwtot ? (int)room : pwtot);
+        int4 *dst = reinterpret_cast<int4 *>(L.out) + wb;
+        const uint32_t ltm = (1u << lane) - 1u;
+        int off = 0;
+#pragma unroll
+        for (int q = 0; q < kX; ++q) {
+            const bool has = (pmask >> q) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, has);
+            const int slot = off + __popc(bal & ltm);
+            if (has && slot < nroom) {
+                // packed best: SNR truncated to 2^-17 and the width's code
+                const int eb = MG ? 64 * (int)((pobk[q >> 2] >> (8 * (q & 3))) & 0xffu) : 0;
+                dst[slot] = make_int4(pdm, psb + (q << psh), (int)(pbits[q] & 0xFFFFFFC0u),
+                                      (int)s_ew[eb + 63 - (int)(pbits[q] & 63u)] << psh);
+            }
+            off += __popc(bal);
+        }
+        pwtot = 0;
+    };
     for (int64_t tile = T0, k = 0; tile < T1; ++tile, ++k) {
         if (k) pos = advance(pos);
         const int ri = pos.ri;
@@ -494,9 +550,15 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
         } else {
             __syncthreads();
         }
+        if (k && tid == kAtomicThread) reserve();
         {
             const int64_t nk = ((int64_t)ri << 32) | (uint32_t)entry;
             if (nk != key) {
+                // the last tile's records read the widths it was searched with
+                if (k) {
+                    __syncthreads();
+                    flush();
+                }
                 if (tid == 0) {
                     s_mu = rd.mu_tab[entry];
                     s_deg = rd.flags[entry];
@@ -506,7 +568,11 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
             }
         }
         if (s_deg) {   // degenerate sigma: no candidates (uniform across the CTA)
+            __syncthreads();
             if (tma && tid == 0 && more) issue(advance(pos));
+            flush();
+            __syncthreads();   // every warp has read its slice before the counts change
+            if (lane == 0) s_wsum[warp] = 0;
             continue;
         }
         if (rd.scale && (((int64_t)ri << 40 | row) != skey)) {
@@ -607,6 +673,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
         __syncthreads();   // (B)
         // the raw buffer is free: fetch the next tile's window
         if (tma && tid == 0 && more) issue(advance(pos));
+        flush();           // the last tile's records, into the slice reserved above
 
         // ---- prefix values at block starts, their maxima, energy prefix
         {
@@ -710,7 +777,8 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
                 }
             }
         };
-        for (int gi = rp.n_groups - 1; gi >= 0; --gi) {
+        // threads past the tile's units only stage (the halo blocks)
+        for (int gi = tid < U ? rp.n_groups - 1 : -1; gi >= 0; --gi) {
             const int4 ga = s_gr[2 * gi];
             const int4 gb = s_gr[2 * gi + 1];
             float rmax;
@@ -822,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
         }
         if (MG && cur_blk >= 0) merge_block();
 
-        // ---- threshold (Sec. 2.4, inclusive) and compaction
+        // ---- threshold (Sec. 2.4, inclusive); the records wait for the next tile
         uint32_t mask = 0;
         if (any) {
             const int64_t ne = rd.n_emit - (t0 + (int64_t)tid * kX);
@@ -834,87 +902,61 @@ __global__ void __launch_bounds__(kThreads, 2) search_kernel(const __grid_consta
             }
             if (lim < kX) mask &= (1u << lim) - 1u;
         }
-        const int cnt = __popc(mask);
-        const int wtot = __reduce_add_sync(0xffffffffu, cnt);
-        if (lane == 0) s_wsum[warp] = wtot;
-        if (!__syncthreads_or(cnt)) continue;   // (E) most tiles of noise-like data
-        if (tid < 32) {
-            const int wv = lane < kThreads / 32 ? s_wsum[lane] : 0;
-            int wsc = wv;
+        pmask = mask;
 #pragma unroll
-            for (int o = 1; o < kThreads / 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, wsc, o);
-                if (lane >= o) wsc += v;
-            }
-            const int total = __shfl_sync(0xffffffffu, wsc, kThreads / 32 - 1);
-            unsigned long long base = 0;
-            if (lane == 0)
-                base = atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
-                                 (unsigned long long)total);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (lane < kThreads / 32) s_wbase[lane] = base + (unsigned long long)(wsc - wv);
-        }
-        __syncthreads();   // (F)
-        if (wtot) {
-            // The warp's records go to its slice of the list start index by
-            // start index: for start q the lanes holding a candidate there
-            // write consecutive slots (rank among them by ballot), so each
-            // store instruction is one coalesced run of 16-byte records.
-            const unsigned long long wb = s_wbase[warp];
-            const long long room = (long long)L.capacity - (long long)wb;
-            const int nroom = room <= 0 ? 0 : (room < wtot ? (int)room : wtot);
-            int4 *dst = reinterpret_cast<int4 *>(L.out) + wb;
-            const int dmv = rd.dm_offset + (int)row;
-            const int sh = rd.sample_shift;
-            const int sbase = (int)(rd.sample_base + ((t0 + (int64_t)tid * kX) << sh));
-            const uint32_t lt = (1u << lane) - 1u;
-            int off = 0;
+        for (int q = 0; q < kX; ++q) pbits[q] = __float_as_uint(MG ? ob[q] : cb[q]);
+        if (MG) {
 #pragma unroll
-            for (int q = 0; q < kX; ++q) {
-                const bool has = (mask >> q) & 1u;
-                const uint32_t bal = __ballot_sync(0xffffffffu, has);
-                const int slot = off + __popc(bal & lt);
-                if (has && slot < nroom) {
-                    const float bv = MG ? ob[q] : cb[q];
-                    const uint32_t bits = __float_as_uint(bv);
-                    const int eb = MG ? 64 * (int)((obk[q >> 2] >> (8 * (q & 3))) & 0xffu) : 0;
-                    dst[slot] = make_int4(dmv, sbase + (q << sh), (int)(bits & 0xFFFFFFC0u),
-                                          (int)s_ew[eb + 63 - (int)(bits & 63u)] << sh);
-                }
-                off += __popc(bal);
-            }
+            for (int q = 0; q < kX / 4; ++q) pobk[q] = obk[q];
         }
+        pdm = rd.dm_offset + (int)row;
+        psh = rd.sample_shift;
+        psb = (int)(rd.sample_base + ((t0 + (int64_t)tid * kX) << psh));
+        pwtot = __reduce_add_sync(0xffffffffu, __popc(mask));
+        if (lane == 0) s_wsum[warp] = pwtot;
     }
+    // the last tile's records
+    __syncthreads();
+    if (tid == kAtomicThread) reserve();
+    __syncthreads();
+    flush();
 }
 
-template <int DT, int G>
-cudaError_t launch_sg(const Launch &L, bool mg, size_t smem, int ctas_per_sm, cudaStream_t s) {
+template <int DT, int G, int NT>
+cudaError_t launch_sgn(const Launch &L, bool mg, size_t smem, int ctas_per_sm, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    void (*k)(const Launch) = mg ? search_kernel<DT, G, true> : search_kernel<DT, G, false>;
+    void (*k)(const Launch) = mg ? search_kernel<DT, G, true, NT> : search_kernel<DT, G, false, NT>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const int64_t grid = L.n_tiles < (int64_t)sms * per_sm ? L.n_tiles : (int64_t)sms * per_sm;
-    k<<<(unsigned)grid, kThreads, smem, s>>>(L);
+    k<<<(unsigned)grid, NT, smem, s>>>(L);
     return cudaGetLastError();
+}
+
+template <int DT, int G>
+cudaError_t launch_sg(const Launch &L, bool mg, size_t smem, int ctas_per_sm, int threads,
+                      cudaStream_t s) {
+    return threads == 128 ? launch_sgn<DT, G, 128>(L, mg, smem, ctas_per_sm, s)
+                          : launch_sgn<DT, G, 256>(L, mg, smem, ctas_per_sm, s);
 }
 
 }  // namespace
 
 template <int DT>
 cudaError_t launch_search_dt(const Launch &L, int G, bool multi_block, size_t smem,
-                             int ctas_per_sm, cudaStream_t s) {
+                             int ctas_per_sm, int threads, cudaStream_t s) {
     switch (G) {
-        case 8: return launch_sg<DT, 8>(L, multi_block, smem, ctas_per_sm, s);
-        case 16: return launch_sg<DT, 16>(L, multi_block, smem, ctas_per_sm, s);
-        default: return launch_sg<DT, 1>(L, multi_block, smem, ctas_per_sm, s);
+        case 8: return launch_sg<DT, 8>(L, multi_block, smem, ctas_per_sm, threads, s);
+        case 16: return launch_sg<DT, 16>(L, multi_block, smem, ctas_per_sm, threads, s);
+        default: return launch_sg<DT, 1>(L, multi_block, smem, ctas_per_sm, threads, s);
     }
 }
 
