@@ -125,12 +125,16 @@ typedef struct {
     int32_t reserved0;
 } spd_cluster;
 
-/* Device-side summary written by the candidate-producing calls (16 bytes).
- * count: exact number of samples with SNR >= threshold, even when it exceeds
+/* Device-side summary written by the record-producing calls (16 bytes).
+ * count: the exact number of records the call produced, even when it exceeds
  * the capacity (then only `capacity` records are written, which ones is
- * unspecified); status: SPD_OK, SPD_ERR_DEGENERATE_SIGMA, or SPD_ERR_TIMEOUT
- * (a tile's bulk copy did not land within the kernel's wait bound, 2 s: the
- * kernel stopped instead of waiting on; see spd_debug_set_copy_wait). */
+ * unspecified).  For the search and threshold calls (spd_search, spd_detect,
+ * spd_search_batched, spd_search_decimated, spd_stream_push/flush,
+ * spd_threshold_candidates) that is the number of candidates, samples with
+ * SNR >= threshold; for spd_cluster_rows the number of clusters.
+ * status: SPD_OK, SPD_ERR_DEGENERATE_SIGMA, or SPD_ERR_TIMEOUT (a tile's bulk
+ * copy did not land within the kernel's wait bound, 2 s: the kernel stopped
+ * instead of waiting on; see spd_debug_set_copy_wait). */
 typedef struct {
     uint64_t count;
     int32_t status;
@@ -185,9 +189,12 @@ spd_status spd_msd(const spd_plane *plane, int32_t scope, int32_t nmax_sigma,
  * in device memory; every GPU that loads the library keeps it until the
  * process exits.  Limit: n_dm * ceil(n_samp / SPD_MSD_UNIT_SAMPLES) must not
  * exceed SPD_MSD_NOALLOC_MAX_UNITS (e.g. 4096 x 524288), else the call returns
- * SPD_ERR_NO_MEMORY and launches nothing.  The first call on each device looks
- * up the array's device address (a CUDA runtime query); make that first call
- * before any stream capture.  All calls share the one array: calls whose
+ * SPD_ERR_NO_MEMORY and launches nothing.  Every call made outside stream
+ * capture looks up the array's device address on the current device (a CUDA
+ * runtime query), so a device reset, after which the array may sit elsewhere,
+ * is handled; a call during stream capture uses the address found by the last
+ * call outside capture on that device, so make one call outside capture
+ * first (else SPD_ERR_CUDA).  All calls share the one array: calls whose
  * kernels overlap on the GPU (different streams, or different host threads)
  * race and give wrong results; calls ordered on one stream do not.  Nothing in
  * the array needs clearing between calls -- each call writes every entry it

@@ -2,8 +2,9 @@
 
 For a given batch (the DM ranges' shapes, storage type, width sets,
 thresholds and sigma modes) every candidate launch shape -- persistent CTAs
-per SM and width-group size -- is timed on the device with CUDA events, and
-the fastest is kept.  Results are cached in a JSON file keyed by the device
+per SM, width-group size (widths per pass between bounds) and tile length
+(threads per CTA: a tile is 16 starts per thread less the halo's blocks) --
+is timed on the device with CUDA events, and the fastest is kept.  Results are cached in a JSON file keyed by the device
 and a hash of the batch description, so a serving process tunes once.
 """
 from __future__ import annotations
@@ -13,7 +14,8 @@ import json
 import os
 import statistics
 
-CANDIDATES = [{"ctas_per_sm": c, "group_scale": g} for c in (0, 1) for g in (1, 2, 4)]
+CANDIDATES = [{"ctas_per_sm": c, "group_scale": g, "tile_threads": t}
+              for t in (256, 128) for c in (0, 1) for g in (1, 2, 4)]
 
 
 def batch_key(specs, device_name: str) -> str:

@@ -392,6 +392,15 @@ def cluster_rows(snr, width, threshold, max_gap, capacity, *, n_samp=None, strea
     """spd_cluster_rows: per-DM clusters of the candidates (snr >= threshold),
     a gap of at most max_gap samples joining neighbours; returns (records int32
     [capacity, 8], result uint8 [16]).  Decode with clusters_to_numpy."""
+    # the C ABI reads raw float32 / 16-bit rows at one shared stride
+    if snr.dtype != torch.float32:
+        raise ValueError("snr plane must be float32")
+    if width.dtype not in (torch.int16, torch.uint16):
+        raise ValueError("width plane must be 16-bit (int16 or uint16)")
+    if snr.device != width.device:
+        raise ValueError("snr and width planes must be on the same device")
+    if snr.dim() != 2 or width.dim() != 2 or snr.stride(1) != 1 or width.stride(1) != 1:
+        raise ValueError("snr and width planes must be 2-D with contiguous rows")
     if width.stride(0) != snr.stride(0):
         raise ValueError("snr and width planes must share a row stride")
     lib = load()

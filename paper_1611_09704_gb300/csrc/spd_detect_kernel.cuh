@@ -1,6 +1,7 @@
-// spd_detect_kernel.cuh -- steps (b), (c), (d): boxcar filters, SNR, max over
-// widths with the winning width, and thresholding with compaction (Sec. 2.3-2.4,
-// Algorithm 1).
+// spd_detect_kernel.cuh -- steps (b) and (c) over every sample: the plane
+// output of spd_boxcar_snr, each start's best SNR over the widths and the
+// winning width (Sec. 2.3, Algorithm 1).  The candidate search, which prunes
+// with bounds and writes records, is the search kernel (spd_search_kernel.cuh).
 //
 // Persistent CTAs of 256 threads walk the plane's tiles (kTile = 4096
 // consecutive samples of one DM row).  Each tile's window -- the tile plus the
@@ -8,31 +9,17 @@
 // bulk (TMA) copy issued one tile ahead, so the copy of tile k+1 overlaps the
 // arithmetic of tile k.  The window is then staged as centred values
 // y = x - mu, G-sample window sums S_G, and per 16-position block a
-// compensated (hi + lo) prefix sum of y with the block's largest and smallest
-// prefix value.
+// compensated (hi + lo) prefix sum of y.
 //
 // Each thread owns kX = 16 consecutive start samples and keeps their running
 // boxcar sums B in registers as eight pairs of adjacent samples (one packed
 // f32x2 add or multiply serves two samples).  Widths are taken in groups: a
 // group's sums start from the prefix sums (B_off = C[i+off] - C[i]) and grow
 // one step per width as in Algorithm 1 (B = B + x[...]); SNR = B * (1/sigma_w).
-//
-// Plane output (every sample's best SNR and width): the low 6 mantissa bits of
-// each SNR are replaced by a code (63 - index within a block of 64 widths)
-// before a float max, so one max keeps value and width; among SNRs equal to
-// 2^-17 relative the smallest width wins -- the strict ">" of Algorithm 1 at
-// that resolution.
-//
-// Candidate search: per group only the value max is kept (three-input max,
-// two widths per instruction); the group's index is packed into it instead.
-// Before a group is evaluated, an upper bound of its SNRs over the thread's 16
-// samples -- (max prefix over the positions it reaches - min prefix at the
-// samples) * max 1/sigma_w -- is compared with max(threshold, the smallest
-// current best of the 16 samples); a group that cannot reach either cannot
-// change any candidate and is skipped.  Groups are visited from the widest
-// down.  For the candidates alone the winning group is evaluated again (same
-// arithmetic, so bitwise the same SNRs) to find the first width whose SNR
-// equals the kept maximum -- the same width the plane output reports.
+// The low 6 mantissa bits of each SNR are replaced by a code (63 - index
+// within a block of 64 widths) before a float max, so one max keeps value and
+// width; among SNRs equal to 2^-17 relative the smallest width wins -- the
+// strict ">" of Algorithm 1 at that resolution.
 //
 // Widths past the row end see y = -inf (sums -inf or NaN), ignored by max.
 // Shared arrays hold 16 positions in 20 words (4 padding words per block of
@@ -52,23 +39,6 @@ __device__ __forceinline__ int padr(int p) { return (p & 15) + kPad * (p >> 4); 
 
 // ------------------------------------------------------------ width sinks
 
-// Candidate search: value max of the current group per sample.
-struct MaxSink {
-    float m[kX];
-    __device__ __forceinline__ void reset() {
-#pragma unroll
-        for (int k = 0; k < kX; ++k) m[k] = -INFINITY;
-    }
-    __device__ __forceinline__ void two(int j, int, float2 sa, float2 sb) {
-        m[2 * j] = fmax3(m[2 * j], sa.x, sb.x);
-        m[2 * j + 1] = fmax3(m[2 * j + 1], sa.y, sb.y);
-    }
-    __device__ __forceinline__ void one(int j, int, float2 sa) {
-        m[2 * j] = fmaxf(m[2 * j], sa.x);
-        m[2 * j + 1] = fmaxf(m[2 * j + 1], sa.y);
-    }
-};
-
 // Plane output: packed (SNR, width code) max per sample.
 struct PackSink {
     float best[kX];
@@ -81,29 +51,6 @@ struct PackSink {
         const uint32_t ka = 63u - (uint32_t)(wi & 63);
         best[2 * j] = fmaxf(best[2 * j], packw(sa.x, ka));
         best[2 * j + 1] = fmaxf(best[2 * j + 1], packw(sa.y, ka));
-    }
-};
-
-// Recovery: first eval index whose SNR, packed with the group's code, equals
-// the kept maximum (truncated value | (63 - group)) -- only possible for the
-// samples whose winner lies in the group being re-evaluated.
-struct FindSink {
-    float best[kX];
-    int found[kX];
-    uint32_t code;       // 63 - group
-    __device__ __forceinline__ void test(int k, int wi, float s) {
-        if (found[k] < 0 && __float_as_uint(packw(s, code)) == __float_as_uint(best[k]))
-            found[k] = wi;
-    }
-    __device__ __forceinline__ void two(int j, int wi, float2 sa, float2 sb) {
-        test(2 * j, wi, sa.x);
-        test(2 * j + 1, wi, sa.y);
-        test(2 * j, wi + 1, sb.x);
-        test(2 * j + 1, wi + 1, sb.y);
-    }
-    __device__ __forceinline__ void one(int j, int wi, float2 sa) {
-        test(2 * j, wi, sa.x);
-        test(2 * j + 1, wi, sa.y);
     }
 };
 
@@ -471,38 +418,6 @@ __device__ __forceinline__ void load_range_consts(const RangeDesc &rd, int entry
     }
 }
 
-// Sparse max table of the block prefix maxima: level k (1 <= k <= kmax)
-// holds the maximum of s_mx over blocks [c, c + 2^k) (fewer past the end).
-// Starts and ends with a barrier.
-__device__ __forceinline__ void build_max_table(const float *s_mx, float *s_st, int R, int RM,
-                                                int kmax) {
-    __syncthreads();
-    const int k3 = kmax < 3 ? kmax : 3;
-    for (int c = threadIdx.x; c < R; c += kThreads) {
-        // blocks past the end repeat the last one (max is unchanged by it)
-        const float m1 = fmaxf(s_mx[c], s_mx[min(c + 1, R - 1)]);
-        s_st[c] = m1;
-        if (k3 >= 2) {
-            const float m2 = fmaxf(m1, fmaxf(s_mx[min(c + 2, R - 1)], s_mx[min(c + 3, R - 1)]));
-            s_st[RM + c] = m2;
-            if (k3 >= 3) {
-                float m3 = m2;
-#pragma unroll
-                for (int j = 4; j < 8; ++j) m3 = fmaxf(m3, s_mx[min(c + j, R - 1)]);
-                s_st[2 * RM + c] = m3;
-            }
-        }
-    }
-    for (int k = 4; k <= kmax; ++k) {
-        __syncthreads();
-        const float *lo = s_st + (k - 2) * RM;
-        const int h = 1 << (k - 1);
-        for (int c = threadIdx.x; c < R; c += kThreads)
-            s_st[(k - 1) * RM + c] = fmaxf(lo[c], lo[min(c + h, R - 1)]);
-    }
-    __syncthreads();
-}
-
 template <int DT, int G, bool PLANE, bool MG>
 __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const __grid_constant__ Launch L) {
     using T = typename Elem<DT>::T;
@@ -522,8 +437,6 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
     uint16_t *s_ew = reinterpret_cast<uint16_t *>(s_gb + kMaxCodeGroups);
     __shared__ int s_kmax;
     __shared__ Group s_grp[kMaxCodeGroups];   // the range's width groups
-    __shared__ int s_wsum[kThreads / 32];
-    __shared__ unsigned long long s_base;
     __shared__ float s_wt[3 * (kThreads / 32) + 3 * kThreads];
 
     const int tid = threadIdx.x;
@@ -676,7 +589,6 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
         }
 
         build_stats<G>(s_y, s_g, s_bs, s_mx, s_mn, s_wt, R);   // ends with a barrier
-        if (!PLANE && s_kmax > 0) build_max_table(s_mx, s_st, R, RM, s_kmax);
 
         const float *sy_t = s_y + kPad * tid;
         const float *sg_t = s_g + kPad * tid;
@@ -761,135 +673,6 @@ __global__ void __launch_bounds__(kThreads, 512 / kThreads) detect_kernel(const 
             continue;
         }
 
-        // ------------------------------------------------ candidate search
-        const float thr = rd.threshold;
-        const float minC = s_mn[tid];
-        float best[kX];
-#pragma unroll
-        for (int q = 0; q < kX; ++q) best[q] = -INFINITY;
-        MaxSink mk;
-        float minbest = -INFINITY;   // smallest current best of the 16 samples
-        for (int gi = rp.n_groups - 1; gi >= 0; --gi) {
-            // upper bound over the thread's 16 samples and the group's widths
-            const int4 gb = s_gb[gi];
-            float rmax;
-            if (gb.z >= 0) {
-                const float *lv = gb.z ? s_st + (gb.z - 1) * RM : s_mx;
-                rmax = fmaxf(lv[tid + gb.x], lv[tid + gb.y]);
-            } else {
-                rmax = -INFINITY;
-                for (int jb = tid + gb.x; jb <= tid + gb.y; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
-            }
-            const float lim = fmaxf(thr, minbest);
-            const float ub = __fsub_rn(rmax, minC);
-            const float slack = 1e-5f * (fabsf(rmax) + fabsf(minC)) + 1e-30f;
-            const float bound = ub > 0.f ? (ub + slack) * __int_as_float(gb.w) * 1.00001f : 0.f;
-            // a NaN bound (window past the row end) falls through to evaluation
-            if (bound + 1e-5f * fabsf(lim) < lim) continue;
-            const Group g = s_grp[gi];
-            mk.reset();
-            group_start(B, s_y, s_bs, tid, g.off);
-            run_group<G>(B, mk, sy_t, sg_t, g, s_inv);
-            const uint32_t code = 63u - (uint32_t)gi;
-#pragma unroll
-            for (int q = 0; q < kX; ++q) best[q] = fmaxf(best[q], packw(mk.m[q], code));
-            minbest = best[0];
-#pragma unroll
-            for (int q = 1; q < kX; ++q) minbest = fminf(minbest, best[q]);
-        }
-
-        // Threshold (Sec. 2.4, inclusive): the candidates and their winning groups
-        uint32_t mask = 0;
-        uint64_t need = 0;
-        uint32_t wcode[kX / 4];   // winning group code of sample q: byte q & 3 of wcode[q >> 2]
-        {
-            const int64_t ne = rd.n_emit - i0;   // starts of this unit that may be emitted
-            const int lim = ne <= 0 ? 0 : (ne >= kX ? kX : (int)ne);
-#pragma unroll
-            for (int q = 0; q < kX; ++q)
-                if (q < lim && trunc17(best[q]) >= thr) mask |= 1u << q;
-        }
-#pragma unroll
-        for (int q = 0; q < kX / 4; ++q) wcode[q] = 0;
-        if (mask) {
-#pragma unroll
-            for (int q = 0; q < kX; ++q) {
-                const uint32_t code = __float_as_uint(best[q]) & 63u;
-                wcode[q >> 2] |= code << (8 * (q & 3));
-                if ((mask >> q) & 1u) need |= 1ull << (63u - code);
-            }
-        }
-        // block-aggregated compaction: one atomic per CTA reserves the tile's
-        // records; thread t's records start at idx0
-        const int cnt = __popc(mask);
-        const int lane = tid & 31, warp = tid >> 5;
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        // the barrier that publishes the warp counts also tells whether the
-        // tile has any candidate; most tiles of noise-like data have none
-        if (!__syncthreads_or(cnt)) continue;   // every thread is done with this tile
-        if (tid < 32) {
-            const int wv = (lane < kThreads / 32) ? s_wsum[lane] : 0;
-            int wsc = wv;
-#pragma unroll
-            for (int o = 1; o < kThreads / 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, wsc, o);
-                if (lane >= o) wsc += v;
-            }
-            if (lane < kThreads / 32) s_wsum[lane] = wsc - wv;   // exclusive
-            const int total = __shfl_sync(0xffffffffu, wsc, kThreads / 32 - 1);
-            if (lane == 0)
-                s_base = total ? atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
-                                           (unsigned long long)total)
-                               : 0ull;
-        }
-        __syncthreads();
-        const unsigned long long idx0 = s_base + (unsigned long long)(s_wsum[warp] + incl - cnt);
-
-        // Recovery and emission: each winning group is evaluated again through
-        // the same path (so bitwise the same SNRs), now keeping a packed (SNR,
-        // eval index) max per sample; a group never straddles a multiple of 64
-        // in eval index, so the code bits give the index.  Among SNRs equal to
-        // 2^-17 relative the smallest width wins, as in the plane output.  For
-        // the samples this group won, its maximum truncated to 2^-17 is the
-        // sample's best SNR.
-        while (need) {
-            const int gi = __ffsll((long long)need) - 1;
-            need &= need - 1;
-            const Group g = s_grp[gi];
-            PackSink rk;
-#pragma unroll
-            for (int q = 0; q < kX; ++q) rk.best[q] = -INFINITY;
-            group_start(B, s_y, s_bs, tid, g.off);
-            run_group<G>(B, rk, sy_t, sg_t, g, s_inv);
-            const uint32_t gcode = 63u - (uint32_t)gi;
-            const int base = (g.widx0 & ~63) + 63;
-#pragma unroll
-            for (int q = 0; q < kX; ++q) {
-                if (((mask >> q) & 1u) && ((wcode[q >> 2] >> (8 * (q & 3))) & 63u) == gcode) {
-                    const unsigned long long idx =
-                        idx0 + (unsigned long long)__popc(mask & ((1u << q) - 1u));
-                    if (idx < (unsigned long long)L.capacity) {
-                        int4 rec;
-                        rec.x = rd.dm_offset + (int)row;
-                        rec.y = (int)(rd.sample_base + ((i0 + q) << rd.sample_shift));
-                        rec.z = __float_as_int(trunc17(rk.best[q]));
-                        rec.w = (int)s_ew[base - (int)(__float_as_uint(rk.best[q]) & 63u)]
-                                << rd.sample_shift;
-                        reinterpret_cast<int4 *>(L.out)[idx] = rec;
-                    }
-                }
-            }
-        }
-        // the next tile rewrites the shared arrays that recovery reads: with
-        // bulk copies the barrier after the next copy's wait orders that,
-        // otherwise this one
-        if (!tma) __syncthreads();
     }
 }
 
@@ -901,11 +684,8 @@ cudaError_t launch_dg(const Launch &L, bool plane_out, bool mg, size_t smem, int
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    void (*k)(const Launch);
-    if (plane_out)
-        k = mg ? detect_kernel<DT, G, true, true> : detect_kernel<DT, G, true, false>;
-    else
-        k = detect_kernel<DT, G, false, false>;
+    if (!plane_out) return cudaErrorInvalidValue;   // candidates: the search kernel
+    void (*k)(const Launch) = mg ? detect_kernel<DT, G, true, true> : detect_kernel<DT, G, true, false>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);

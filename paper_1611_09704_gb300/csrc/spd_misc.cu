@@ -147,9 +147,11 @@ struct ClusterState {
 };
 
 // Monotone map of a non-NaN float to an unsigned key (larger float, larger
-// key); every key is > 0, so 0 stands for "no member".
+// key; -0.0 and +0.0 compare equal, so they share one key); every key is
+// > 0, so 0 stands for "no member".
 __device__ __forceinline__ unsigned order_key(float f) {
-    const unsigned u = __float_as_uint(f);
+    unsigned u = __float_as_uint(f);
+    if (u == 0x80000000u) u = 0u;
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 

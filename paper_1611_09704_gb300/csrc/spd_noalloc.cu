@@ -13,10 +13,12 @@
 //
 // The array is loaded with the library on every GPU that uses it and stays
 // allocated until the process exits.  Host code must not use the array's name
-// as a device address (it is a host-side stand-in): the address is fetched
-// with cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on that device.  That first call therefore makes a CUDA
-// runtime query and should come before any stream capture.
+// as a device address (it is a host-side stand-in): the address comes from
+// cudaGetSymbolAddress with the device current.  Every call made outside
+// stream capture looks it up again, so a device reset (after which the array
+// may sit elsewhere) is handled; a call during stream capture uses the
+// address found by the last call outside capture on that device, so one call
+// outside capture must come first.
 #include "spd_internal.cuh"
 
 #include <mutex>
@@ -38,18 +40,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};
 
-// Device address of g_msd_scratch on the current device (set-up on first use).
-cudaError_t scratch_address(void **out) {
+// Device address of g_msd_scratch on the current device: looked up on every
+// call outside stream capture (and remembered), the remembered one during
+// capture.
+cudaError_t scratch_address(cudaStream_t st, void **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_msd_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = p;
+    } else if (!g_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;   // no call outside capture yet
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -77,12 +86,12 @@ extern "C" spd_status spd_msd_noalloc(const spd_plane *plane, int32_t scope,
     if (units > SPD_MSD_NOALLOC_MAX_UNITS) return SPD_ERR_NO_MEMORY;   // beyond the static array
     if (scope == SPD_MSD_PER_ROW && plane->n_dm == 0) return SPD_OK;
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    cudaError_t e = scratch_address(st, &base);
     if (e != cudaSuccess) { spd::note_cuda_error((int)e); return SPD_ERR_CUDA; }
     spd::MsdPart *parts = static_cast<spd::MsdPart *>(base);
     spd::MsdPart *slots = parts + SPD_MSD_NOALLOC_MAX_UNITS;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     // Every partial and slot read below is written earlier in this call, so
     // nothing left in the array by a previous call is used.

@@ -31,12 +31,13 @@ def test_cache_round_trip(tmp_path, monkeypatch):
 
     def timer(specs, cap, cand, reps):
         calls.append(cand)
-        return 1.0 + cand["group_scale"] + 0.5 * cand["ctas_per_sm"]
+        return 1.0 + cand["group_scale"] + 0.5 * cand["ctas_per_sm"] + (cand["tile_threads"] == 128)
 
     monkeypatch.setattr(torch.cuda, "get_device_name", lambda d=None: "fake")
     specs = [_spec(2, 50, [1, 2, 3])]
     r = autotune.autotune(specs, 10, cache_path=path, timer=timer)
-    assert r["tuning"] == {"ctas_per_sm": 0, "group_scale": 1} and not r["cached"]
+    assert r["tuning"] == {"ctas_per_sm": 0, "group_scale": 1, "tile_threads": 256}
+    assert not r["cached"]
     assert len(calls) == len(autotune.CANDIDATES)
     r2 = autotune.autotune(specs, 10, cache_path=path, timer=timer)
     assert r2["cached"] and len(calls) == len(autotune.CANDIDATES)

@@ -107,3 +107,22 @@ def test_empty_and_bad_arguments(spd):
     with pytest.raises(spd.SpdError):
         spd.cluster_rows(snr, width, float("nan"), 2, 16)
     torch.cuda.synchronize()
+
+
+def test_signed_zeros_keep_the_earliest_peak(spd):
+    """-0.0 and +0.0 are equal SNRs: with a threshold of 0 the earlier of the
+    two stays the cluster's peak (strict ">" keeps the first among equals)."""
+    n = 64
+    s = np.full((2, n), -1.0, dtype=np.float32)
+    s[0, 10], s[0, 11] = -0.0, 0.0          # -0.0 first
+    s[1, 20], s[1, 21] = 0.0, -0.0          # +0.0 first
+    w = np.arange(1, 2 * n + 1, dtype=np.uint16).reshape(2, n)
+    snr = torch.from_numpy(s).to(DEV)
+    width = torch.from_numpy(w.view(np.int16)).to(DEV)
+    out, res = spd.cluster_rows(snr, width, 0.0, 4, 64)
+    count, status = spd.read_result(res)
+    assert status == 0 and count == 2
+    got = _sorted(spd.clusters_to_numpy(out, count))
+    want = oracle.cluster_rows(s, w, 0.0, 4)
+    assert list(want["peak_sample"]) == [10, 20]
+    _compare(got, want)

@@ -632,3 +632,12 @@ def test_search_decimated_noise_scaling_and_aligned_tophat():
     top = hit[np.argmax(hit["snr"])]
     assert top["sample"] == t0 and top["width"] == w << level
     assert abs(top["snr"] - snr) < 4.0
+
+
+def test_cluster_rows_signed_zeros():
+    """-0.0 and +0.0 are equal: the earlier stays the peak whichever comes first."""
+    best = np.array([[-1.0, -0.0, 0.0, -1.0, 0.0, -0.0]])
+    width = np.arange(1, 7).reshape(1, 6)
+    c = oracle.cluster_rows(best, width, 0.0, 1)
+    assert list(c["first"]) == [1, 4] and list(c["peak_sample"]) == [1, 4]
+    assert list(c["peak_width"]) == [2, 5]

@@ -2,7 +2,8 @@
 library a workspace (for instance a real-time backend that fixes its device
 memory at start-up and must not call cudaMalloc later).  Its block partials
 live in a static device array inside the library; its results must equal
-spd_msd's, call after call.
+spd_msd's, call after call, and meet the MSD tolerance against the FP64
+oracle's two-pass definition.
 
 This file is collected last, so a run that stops at its first failure has
 already run every other test.
@@ -52,18 +53,23 @@ def _close(a, b):
 
 @pytest.mark.parametrize("scope", [0, 1])
 def test_noalloc_matches_workspace_msd_twice(lib, scope):
+    import oracle
     import paper_1611_09704_gb300 as spd
     import synth
+    from tests import _parity as P
     planes = [synth.ska_like(64, 200003, n_pulses=8, device=DEV, seed=31).data,
               synth.plain_tophat(48, 65536, device=DEV, seed=32).data[:, :65000]]
     for x in planes:
         n_samp = x.shape[1]
         ref = spd.msd_to_numpy(spd.msd(x, scope, n_samp=n_samp))
+        mean_o, sd_o = oracle.plane_msd(synth.to_host_numpy(x.contiguous()), scope)
         for _ in range(2):          # two calls in a row share the static array
             rc, out = _noalloc(lib, x, scope, n_samp=n_samp)
             assert rc == 0
             torch.cuda.synchronize()
-            _close(spd.msd_to_numpy(out), ref)
+            got = spd.msd_to_numpy(out)
+            _close(got, ref)
+            P.check_msd(got, mean_o, sd_o)
 
 
 def test_noalloc_limit_and_empty(lib):
