@@ -476,6 +476,28 @@ spd_status spd_search_decimated(const spd_plane *plane, const spd_level *levels,
  * default.  Errors: SPD_ERR_INVALID_ARG. */
 spd_status spd_debug_set_copy_wait(uint64_t limit_ns, uint32_t extra_bytes);
 
+/* ------------------------------------------------------ de-dispersion
+ * The detector runs on de-dispersed data (Sec. 1: the DM x time plane that
+ * the pipeline's de-dispersion step produces; Sec. 3 names coupling the
+ * search to that step as future work).  This is the plain incoherent
+ * de-dispersion that produces such a plane, so that a producer can write DM
+ * trials straight into a streaming search's chunk view
+ * (spd_stream_chunk_view) and the push reads them in place:
+ *   out[d][t] = sum over channels c of x[c][t + delays[d * n_chan + c]],
+ * t < n_out, summed in FP32 in channel order.
+ * fb: the filterbank as a plane of n_chan = fb->n_dm channel rows of
+ * fb->n_samp samples (any storage type, with optional per-channel scale and
+ * offset as for the search).  delays: device int32 [n_dm][n_chan] in samples,
+ * each in 0 .. fb->n_samp - n_out; a delay outside that range makes the
+ * channel add NaN to the output sample (nothing is read outside the row) and
+ * sets status_dev->status (optional, device) to SPD_ERR_INVALID_ARG.
+ * out: device plane [n_dm][out_stride] of out_dtype (FP32, or FP16 / BF16
+ * rounded from the FP32 sum), out_stride >= n_out.  Errors:
+ * SPD_ERR_INVALID_ARG (bad sizes or pointers), SPD_ERR_CUDA. */
+spd_status spd_dedisperse(const spd_plane *fb, const int32_t *delays, int64_t n_dm, void *out,
+                          int32_t out_dtype, int64_t n_out, int64_t out_stride,
+                          spd_result *status_dev, void *stream);
+
 /* Test aid: raw boxcar sums B_w(i) (no centring, no scaling) for one width,
  * NaN where i + w > n_samp.  out: float [n_dm][out_stride] (device). */
 spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out,

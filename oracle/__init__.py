@@ -82,6 +82,8 @@ def _load():
     lib.oracle_num_threads.restype = I32
     lib.oracle_snr_at.argtypes = [P, I32, I64, I64, P, P, I64, I64, I32, D, D]
     lib.oracle_snr_at.restype = D
+    lib.oracle_dedisperse.argtypes = [P, I32, I64, I64, I64, P, P, P, I64, I64, P]
+    lib.oracle_dedisperse.restype = I32
     _lib = lib
     return lib
 
@@ -326,6 +328,23 @@ def cluster_rows(best, width, thr: float, max_gap: int, row0: int = 0):
     for k, c in enumerate(recs):
         for f in out.dtype.names:
             out[k][f] = c[f]
+    return out
+
+
+# ------------------------------------------------------------ de-dispersion
+
+def dedisperse(fb, delays, n_out: int) -> np.ndarray:
+    """The DM x time plane of a filterbank (Sec. 1: the detector's input):
+    out[d, t] = sum over channels c of fb[c, t + delays[d, c]], FP64.
+    fb: a Plane (or array) of channel rows; delays: int [n_dm, n_chan]."""
+    p = as_plane(fb)
+    dl = np.ascontiguousarray(delays, dtype=np.int32)
+    if dl.ndim != 2 or dl.shape[1] != p.n_dm:
+        raise ValueError("delays must be [n_dm, n_chan]")
+    out = np.empty((dl.shape[0], int(n_out)), dtype=np.float64)
+    rc = _load().oracle_dedisperse(*p.args(), _ptr(dl), dl.shape[0], int(n_out), _ptr(out))
+    if rc:
+        raise ValueError("delay outside 0 .. n_samp - n_out")
     return out
 
 

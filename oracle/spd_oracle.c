@@ -19,7 +19,10 @@
  *   - per-sample highest SNR over boxcar widths with the winning width:
  *     Algorithm 1 of Sec. 2.3, boxcar grown one sample at a time, strict ">";
  *   - candidate selection: keep x_i >= f_T (Sec. 2.4), unordered list
- *     returned here in (dm, sample) order.
+ *     returned here in (dm, sample) order;
+ *   - the detector's input, the de-dispersed DM x time plane (Sec. 1): the
+ *     definition of incoherent de-dispersion, a sum over frequency channels
+ *     each shifted by its delay for the DM trial.
  *
  * Readings of silent or garbled points (each is pinned by a test):
  *   - Eq. 1's S update is read with the square, (j x_j - T_j)^2/(j(j-1)),
@@ -446,4 +449,30 @@ double oracle_snr_at(const void *data, int dtype, int64_t n_samp, int64_t stride
     for (int k = 0; k < w; ++k)
         b += sample_value(data, dtype, stride, scale, offset, r, i + k);
     return (b - (double)w * mean) / sigma_w;
+}
+
+/* Incoherent de-dispersion, the step that produces the DM x time plane the
+ * detector searches (Sec. 1), written as its definition: for DM trial d and
+ * output sample t, the sum over channels c of the channel's value at
+ * t + delays[d * n_chan + c], in FP64 in channel order.  The filterbank is a
+ * "plane" of n_chan channel rows.  Returns -1 (and writes nothing) if a delay
+ * lies outside 0 .. n_samp - n_out. */
+int oracle_dedisperse(const void *data, int dtype, int64_t n_chan, int64_t n_samp,
+                      int64_t stride, const float *scale, const float *offset,
+                      const int32_t *delays, int64_t n_dm, int64_t n_out, double *out)
+{
+    if (n_out < 0 || n_out > n_samp) return -1;
+    for (int64_t k = 0; k < n_dm * n_chan; ++k)
+        if (delays[k] < 0 || (int64_t)delays[k] > n_samp - n_out) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t d = 0; d < n_dm; ++d) {
+        for (int64_t t = 0; t < n_out; ++t) {
+            double s = 0.0;
+            for (int64_t c = 0; c < n_chan; ++c)
+                s += sample_value(data, dtype, stride, scale, offset, c,
+                                  t + (int64_t)delays[d * n_chan + c]);
+            out[d * n_out + t] = s;
+        }
+    }
+    return 0;
 }

@@ -108,7 +108,7 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
            "spd_sd_nmax_merge_partials", "spd_threshold_plane",
            "spd_search_decimated_workspace_bytes", "spd_search_decimated",
-           "spd_debug_set_copy_wait", "spd_cluster_rows"]
+           "spd_debug_set_copy_wait", "spd_cluster_rows", "spd_dedisperse"]
 
 
 class SpdError(RuntimeError):
@@ -167,6 +167,8 @@ def load(path: str | None = None):
     lib.spd_search.restype = I32
     lib.spd_boxcar_sums.argtypes = [pp, I32, P, I64, P]
     lib.spd_boxcar_sums.restype = I32
+    lib.spd_dedisperse.argtypes = [pp, P, I64, P, I32, I64, I64, P, P]
+    lib.spd_dedisperse.restype = I32
     pr = ctypes.POINTER(SpdRange)
     pt = ctypes.POINTER(SpdTuning)
     lib.spd_search_batched_workspace_bytes.argtypes = [pr, I32, pt]
@@ -494,6 +496,28 @@ def debug_set_copy_wait(limit_ns=2_000_000_000, extra_bytes=0):
     run out); the defaults restore normal operation."""
     _check(load().spd_debug_set_copy_wait(int(limit_ns), int(extra_bytes)),
            "spd_debug_set_copy_wait")
+
+
+def dedisperse(fb, delays, n_out, *, out=None, out_dtype=F32, status=None, stream=None, **kw):
+    """spd_dedisperse: the DM x time plane of a filterbank (channel rows),
+    out[d, t] = sum over channels c of fb[c, t + delays[d, c]].  ``delays``:
+    device int32 [n_dm, n_chan]; ``out``: a [n_dm, n_out] device tensor with
+    contiguous rows (e.g. BeamStream.chunk_view), made when None."""
+    lib = load()
+    pl = as_plane(fb, **kw)
+    cp = pl.c()
+    if not (isinstance(delays, torch.Tensor) and delays.dtype == torch.int32
+            and delays.is_contiguous() and delays.dim() == 2):
+        raise ValueError("delays must be a contiguous int32 [n_dm, n_chan] tensor")
+    n_dm = delays.shape[0]
+    if out is None:
+        out = torch.empty((n_dm, int(n_out)), dtype=_TD[out_dtype], device=pl.data.device)
+    dt = {v: k for k, v in _TD.items()}.get(out.dtype)
+    if dt is None or out.dim() != 2 or out.stride(1) != 1 or out.shape[0] != n_dm:
+        raise ValueError("out must be [n_dm, >= n_out] f32/f16/bf16 with contiguous rows")
+    _check(lib.spd_dedisperse(ctypes.byref(cp), _ptr(delays), n_dm, _ptr(out), dt, int(n_out),
+                              out.stride(0), _ptr(status), _stream(stream)), "spd_dedisperse")
+    return out
 
 
 def boxcar_sums(x, w, *, stream=None, out=None, **kw):

@@ -310,3 +310,48 @@ def serving_beams(n_beams=16, n_dm=2048, chunks_per_beam=4, *, length_range=(819
             a += L
         out.append(ServingBeam(b, chunks, lengths, pulses))
     return out
+
+
+# Filterbanks for the de-dispersion producer: channel rows of noise with
+# pulses dispersed as a cold plasma does (delay proportional to DM / f^2).
+K_DM_S = 4.148808e3   # dispersion constant, s MHz^2 pc^-1 cm^3
+
+
+def dispersion_delays(n_chan: int, dms, f_lo_mhz: float = 1200.0, f_hi_mhz: float = 1500.0,
+                      t_samp: float = SAMPLE_TIME_S) -> np.ndarray:
+    """Integer delays [n_dm, n_chan] (samples) of each channel relative to the
+    highest frequency, channels ordered from f_hi down to f_lo."""
+    f = np.linspace(f_hi_mhz, f_lo_mhz, n_chan)
+    dms = np.asarray(dms, dtype=np.float64).reshape(-1, 1)
+    dt = K_DM_S * dms * (f.reshape(1, -1) ** -2 - f_hi_mhz ** -2) / t_samp
+    return np.rint(dt).astype(np.int32)
+
+
+@dataclass
+class Filterbank:
+    data: torch.Tensor        # [n_chan, n_samp] float32
+    delays: np.ndarray        # [n_dm, n_chan] int32
+    n_out: int                # de-dispersed samples per DM trial
+    pulses: list              # (dm trial, start sample in the DM x time plane, width, amp)
+
+
+def filterbank(n_chan=64, n_samp=20000, dms=None, *, pulses=((5, 3000, 8, 2.0),),
+               sd=1.0, device="cpu", seed=1611_7) -> Filterbank:
+    """N(0, sd^2) channel noise with top-hat pulses, each dispersed exactly
+    along one DM trial's delays: pulse (k, t0, w, amp) adds amp to channel c
+    at samples t0 + delays[k, c] .. + w - 1, so the de-dispersed trial k holds
+    a top-hat of height n_chan * amp at t0 .. t0 + w - 1."""
+    if dms is None:
+        dms = np.linspace(0.0, 40.0, 16)
+    delays = dispersion_delays(n_chan, dms)
+    n_out = n_samp - int(delays.max())
+    if n_out <= 0:
+        raise ValueError("filterbank shorter than the largest delay")
+    g = _gen(device, seed)
+    data = torch.empty((n_chan, n_samp), dtype=torch.float32, device=device)
+    data.normal_(0.0, sd, generator=g)
+    for (k, t0, w, amp) in pulses:
+        for c in range(n_chan):
+            a = int(t0 + delays[k, c])
+            data[c, a:min(n_samp, a + w)] += amp
+    return Filterbank(data, delays, n_out, list(pulses))

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -641,3 +642,63 @@ def test_cluster_rows_signed_zeros():
     c = oracle.cluster_rows(best, width, 0.0, 1)
     assert list(c["first"]) == [1, 4] and list(c["peak_sample"]) == [1, 4]
     assert list(c["peak_width"]) == [2, 5]
+
+
+# ------------------------------------------------------------ de-dispersion
+
+def test_dedisperse_impulse_response():
+    """One unit sample in channel c0 at time T shows up in DM trial d exactly
+    at t = T - delay[d, c0] (and nowhere else)."""
+    rng = np.random.default_rng(3)
+    n_chan, n_samp, n_out = 5, 60, 45
+    delays = rng.integers(0, n_samp - n_out + 1, size=(4, n_chan)).astype(np.int32)
+    x = np.zeros((n_chan, n_samp), dtype=np.float32)
+    c0, T = 2, 30
+    x[c0, T] = 1.0
+    out = oracle.dedisperse(x, delays, n_out)
+    for d in range(4):
+        want = np.zeros(n_out)
+        t = T - delays[d, c0]
+        if 0 <= t < n_out:
+            want[t] = 1.0
+        assert np.array_equal(out[d], want)
+
+
+def test_dedisperse_zero_delays_sum_channels():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((7, 40)).astype(np.float32)
+    out = oracle.dedisperse(x, np.zeros((2, 7), np.int32), 40)
+    assert np.allclose(out[0], x.astype(np.float64).sum(axis=0), rtol=0, atol=1e-12)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_dedisperse_against_fancy_indexing():
+    """An independent statement of the definition by numpy gathers."""
+    rng = np.random.default_rng(5)
+    n_chan, n_samp, n_out, n_dm = 6, 80, 50, 9
+    x = rng.standard_normal((n_chan, n_samp)).astype(np.float32)
+    delays = rng.integers(0, n_samp - n_out + 1, size=(n_dm, n_chan)).astype(np.int32)
+    t = np.arange(n_out)
+    want = np.stack([x[np.arange(n_chan)[:, None], t[None, :] + delays[d][:, None]]
+                     .astype(np.float64).sum(axis=0) for d in range(n_dm)])
+    assert np.allclose(oracle.dedisperse(x, delays, n_out), want, rtol=0, atol=1e-12)
+
+
+def test_dedisperse_restores_a_dispersed_pulse():
+    """A noise-free top-hat dispersed along trial k: trial k holds n_chan * amp
+    over the pulse's samples; other trials hold less at every sample."""
+    fb = synth.filterbank(16, 4000, dms=np.linspace(0, 30, 8), pulses=((5, 700, 6, 1.5),),
+                          sd=0.0)
+    out = oracle.dedisperse(synth.to_host_numpy(fb.data), fb.delays, fb.n_out)
+    want = np.zeros(fb.n_out)
+    want[700:706] = 16 * 1.5
+    assert np.allclose(out[5], want)
+    assert np.all(np.delete(out, 5, axis=0).max(axis=1) < 16 * 1.5)
+
+
+def test_dedisperse_rejects_out_of_range_delays():
+    x = np.zeros((3, 20), dtype=np.float32)
+    with pytest.raises(ValueError):
+        oracle.dedisperse(x, np.array([[0, 6, 0]], np.int32), 15)
+    with pytest.raises(ValueError):
+        oracle.dedisperse(x, np.array([[0, -1, 0]], np.int32), 10)
