@@ -17,6 +17,7 @@ plane (independent chunks, weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -37,9 +38,8 @@ THRESHOLD = 7.0
 SAMPLE_TIME_S = 64e-6
 # msd_partial, msd_merge_l1, fold_final, merge_shards, consts, detect
 KERNELS_PER_STEP = 6
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "detect_traffic.txt")
-E2E_DEPTH = 3          # planes in flight in the end-to-end measurement
-DETECT_SRC = os.path.join(ROOT, "paper_1611_09704_gb300", "csrc", "spd_detect_kernel.cuh")
+PROFILES = os.path.join(ROOT, "profiles")
+DETECT_SRC = os.path.join(ROOT, "paper_1611_09704_gb300", "csrc", "spd_search_kernel.cuh")
 
 
 def parse():
@@ -56,14 +56,16 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched", "serving",
-                                           "decimated", "cluster"],
+                                           "decimated", "cluster", "plane", "dedisperse"],
                     default="ska",
                     help="ska: the SKA-like FP32 chunk (default, the headline); plain: 64 x 65536 "
                          "FP32 noise + top-hats; precision: the SKA-like chunk stored as FP16 / "
                          "BF16 with Eq. 5; batched: four decimated DM ranges in one launch; "
                          "serving: 16 beams of FP16 chunks streamed with continuous batching; "
                          "decimated: widths to 512 by decimation in time vs the plain search; "
-                         "cluster: per-DM clustering of the SKA-like chunk's candidates")
+                         "cluster: per-DM clustering of the SKA-like chunk's candidates; "
+                         "plane: the unfused calls on the SKA-like chunk (spd_boxcar_snr, "
+                         "spd_threshold_candidates); dedisperse: the de-dispersion producer")
     ap.add_argument("--beams", type=int, default=16)
     ap.add_argument("--chunks-per-beam", type=int, default=3)
     ap.add_argument("--slots", type=int, default=4)
@@ -88,12 +90,16 @@ def detect_source_sha() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _recorded():
-    """The committed ncu record of one detect launch, or None when absent or
-    taken on a different kernel source."""
+def traffic_file(workload: str) -> str:
+    return os.path.join(PROFILES, f"traffic_search_{workload}.txt")
+
+
+def _recorded(workload: str = "ska_like"):
+    """The committed ncu record of one search-kernel launch on `workload`, or
+    None when absent or taken on a different kernel source."""
     try:
         kv = {}
-        with open(TRAFFIC_FILE) as f:
+        with open(traffic_file(workload)) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
@@ -103,10 +109,10 @@ def _recorded():
         return None
 
 
-def recorded_traffic(n_samples: int, n_cand: int):
-    """DRAM bytes per detect launch from the committed ncu record, scaled to
+def recorded_traffic(n_samples: int, n_cand: int, workload: str = "ska_like"):
+    """DRAM bytes per search launch from the committed ncu record, scaled to
     this launch (reads by samples, writes by candidates); None without one."""
-    kv = _recorded()
+    kv = _recorded(workload)
     if kv is None:
         return None
     read = float(kv["dram_read_bytes"]) * n_samples / float(kv["samples"])
@@ -114,13 +120,53 @@ def recorded_traffic(n_samples: int, n_cand: int):
     return int(read + write)
 
 
-def recorded_instructions(n_samples: int):
-    """Issued warp instructions per detect launch from the committed ncu
+def recorded_instructions(n_samples: int, workload: str = "ska_like"):
+    """Issued warp instructions per search launch from the committed ncu
     record, scaled by samples (same data recipe); None without one."""
-    kv = _recorded()
+    kv = _recorded(workload)
     if kv is None or "warp_instructions" not in kv:
         return None
     return float(kv["warp_instructions"]) * n_samples / float(kv["samples"])
+
+
+def hbm_roofline(kernel: str, alg_bytes: float, ms: float, traffic=None, note=None):
+    """Roofline object of one kernel (or step) bound by HBM: algorithmic bytes
+    over the CUDA-event time, against the measured copy bandwidth."""
+    hbm, kind = peaks()
+    ach = alg_bytes / (ms / 1e3) / 1e9
+    r = {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
+         "frac": ach / hbm, "traffic": traffic, "peak_source": f"{kind} hbm_gbs",
+         "algorithmic_bytes": int(alg_bytes), "ms": ms}
+    if note:
+        r["note"] = note
+    return r
+
+
+def sm_max_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz") or 2070.0)
+    except (OSError, ValueError):
+        return 2070.0
+
+
+def alu_roofline(kernel: str, ops: float, ms: float, note=None):
+    """Roofline object of a kernel bound by FP32 arithmetic: algorithmic
+    operations over the CUDA-event time, against SMs x 128 FP32 lanes x 2
+    (packed f32x2 add / multiply) x the measured maximum SM clock."""
+    mhz = sm_max_mhz()
+    peak = SM_COUNT * 128 * 2 * mhz * 1e6 / 1e12
+    ach = ops / (ms / 1e3) / 1e12
+    r = {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "Tops/s",
+         "frac": ach / peak, "traffic": None,
+         "peak_source": f"{SM_COUNT} SMs x 128 lanes x 2 (f32x2) x {mhz:.0f} MHz",
+         "algorithmic_ops": ops, "ms": ms}
+    if note:
+        r["note"] = note
+    return r
+
+
+SM_COUNT, SCHEDULERS_PER_SM = 152, 4
 
 
 class Clocks:
@@ -181,9 +227,6 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
-
-
-SM_COUNT, SCHEDULERS_PER_SM = 152, 4
 
 
 def issue_roofline(n_samples: int, det_ms: float):
@@ -343,7 +386,6 @@ def run_spd(a, rank, world, local):
 
     hbm, peak_kind = peaks()
     det_bytes = n * 4 + 16 * count
-    achieved = det_bytes / (det_ms / 1e3) / 1e9
     traffic = recorded_traffic(n, count)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -351,11 +393,8 @@ def run_spd(a, rank, world, local):
             "config": workload_config(n_dm, n_samp, world),
             "realtime_factor": n_samp * SAMPLE_TIME_S / (ms_step / 1e3),
             "candidates_per_step": count,
-            "roofline": {"bound": "hbm", "kernel": "detect (boxcar+SNR+max+threshold)",
-                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "peak_source": f"{peak_kind} hbm_gbs",
-                         "algorithmic_bytes": det_bytes, "ms": det_ms},
+            "roofline": hbm_roofline("search_kernel (boxcar + SNR + max + threshold)",
+                                     det_bytes, det_ms, traffic),
             "issue_roofline": issue_roofline(n, det_ms),
             "step_breakdown_ms": {"msd": msd_ms, "detect": det_ms},
             "whole_step_hbm_frac": (2 * n * 4 + 16 * count) / (ms_step / 1e3) / 1e9 / hbm,
@@ -376,52 +415,72 @@ def run_spd(a, rank, world, local):
 
 
 def e2e(x, count, steps, n, world, rank, dev):
-    """Planes searched from page-locked host memory through PlanePipeline:
-    every step copies its plane in, runs the sharded search and copies its
-    count and every candidate record out; two planes in flight overlap one
-    plane's copy out with the next one's copy in and search.  Whole-run time
-    (fill and drain included) / steps, slowest rank."""
+    """Planes searched from page-locked host memory through spd_search_host,
+    the C-ABI call with host buffers: every call copies its plane in, computes
+    the MSD and searches, and returns with every candidate record and the
+    count in host memory.  Two host threads call it with their own stream and
+    workspace, so one plane's copy in overlaps the other's copy out.
+    Whole-run wall time / planes, slowest rank (each rank's plane its own
+    dataset: MSD per plane)."""
+    import threading
+
     import torch
     import torch.distributed as dist
 
-    from paper_1611_09704_gb300.pipeline import PlanePipeline
+    import paper_1611_09704_gb300 as spd
+    local = dev.index if dev.index is not None else 0
     xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
     xh.copy_(x)
-    n_dm, n_samp = x.shape
-    cap = int(n * 0.45) + 1024
-    depth = E2E_DEPTH
-    pp = PlanePipeline(n_dm, n_samp, WIDTHS, THRESHOLD, cap, dtype=x.dtype, depth=depth,
-                       device=dev, dm_offset=rank * n_dm,
-                       host_capacity=count + (count >> 4) + 1024)
-    # one untimed plane (lazy set-up, page-in of the host buffers)
-    r = pp.collect(pp.submit(xh))
-    if r[0] != count:
-        raise RuntimeError(f"pipeline count {r[0]} != {count}")
-    d2h = []
+    cap = count + (count >> 4) + 1024
+    n_workers = 2
+    ws = [torch.empty(spd.search_host_workspace_bytes(xh, WIDTHS, THRESHOLD, cap),
+                      dtype=torch.uint8, device=dev) for _ in range(n_workers)]
+    outs = [torch.empty((cap, 4), dtype=torch.int32, pin_memory=True) for _ in range(n_workers)]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_workers)]
+    counts = [[] for _ in range(n_workers)]
+    errors = []
+
+    def worker(w, planes):
+        try:
+            torch.cuda.set_device(local)
+            for _ in range(planes):
+                c, st = spd.search_host(xh, WIDTHS, THRESHOLD, outs[w], workspace=ws[w],
+                                        stream=streams[w])
+                if st != 0 or c != count:
+                    raise RuntimeError(f"spd_search_host: count {c} status {st}")
+                counts[w].append(c)
+        except Exception as e:   # reported by the caller
+            errors.append(e)
+
+    def run(planes):
+        th = [threading.Thread(target=worker, args=(w, planes // n_workers + (w < planes % n_workers)))
+              for w in range(n_workers)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errors:
+            raise errors[0]
+
+    run(n_workers)          # untimed: set-up, page-in of the host buffers
+    for c in counts:
+        c.clear()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tickets = [pp.submit(xh) for _ in range(min(depth, steps))]
-    for k in range(steps):
-        c, st, recs = pp.collect(tickets[k])
-        if st != 0:
-            raise RuntimeError(f"pipeline status {st}")
-        d2h.append(16 + 16 * recs.shape[0])
-        if k + depth < steps:
-            tickets.append(pp.submit(xh))
+    run(steps)
     t = (time.perf_counter() - t0) / steps
     if world > 1:
         tt = torch.tensor([t], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = float(tt.item())
-    del pp
+    del ws, outs
     torch.cuda.empty_cache()
     return {"value": world * n / t, "unit": UNIT, "h2d_bytes_per_step": n * x.element_size(),
-            "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3,
-            "steps": steps,
-            "api": f"PlanePipeline (sharded search over the C ABI) from page-locked host "
-                   f"memory, {depth} planes in flight"}
+            "d2h_bytes_per_step": 16 + 16 * count, "ms_per_step": t * 1e3, "steps": steps,
+            "api": f"spd_search_host (C ABI, host buffers: page-locked plane in, records and "
+                   f"count out) from {n_workers} host threads"}
 
 
 def timed(step, steps, warmup, clocks_dev):
@@ -441,9 +500,35 @@ def timed(step, steps, warmup, clocks_dev):
     return e0.elapsed_time(e1) / steps, clk.stop()
 
 
+def timed_split(phases, steps, warmup, clocks_dev):
+    """Warm up, then time `steps` passes of the phases (callables run in
+    order) with CUDA events between them on the current stream: returns
+    (total ms per step, [ms per step of each phase], clocks)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        for f in phases:
+            f()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
+          for _ in range(steps)]
+    clk = Clocks(clocks_dev)
+    for k in range(steps):
+        ev[k][0].record()
+        for j, f in enumerate(phases):
+            f()
+            ev[k][j + 1].record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    per = [statistics.mean(e[j].elapsed_time(e[j + 1]) for e in ev) for j in range(len(phases))]
+    total = statistics.mean(e[0].elapsed_time(e[-1]) for e in ev)
+    return total, per, clocks
+
+
 def run_other(a):
     """The other configurations of the search, one JSON line each."""
     import torch
+
+    import numpy as np
 
     import paper_1611_09704_gb300 as spd
     import synth
@@ -473,6 +558,9 @@ def run_other(a):
         count = spd.read_result(res)[0]
         line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
                     candidates_per_step=count, gpu_launches=5 * a.steps,
+                    roofline=hbm_roofline("search step (MSD + search kernel)",
+                                          2 * 4 * n + 16 * count, ms,
+                                          note="inputs L2-resident (16.8 MB): latency-bound"),
                     realtime_factor=65536 * SAMPLE_TIME_S / (ms / 1e3),
                     config={"workload": "plain FP32 64 DM x 65536, N(0,1) + top-hats "
                                         "{1,3,8,17,30}; widths 1..32; f_T 6; sqrt(N) sigma",
@@ -493,23 +581,35 @@ def run_other(a):
         res = torch.zeros(16, dtype=torch.uint8, device=dev)
         msd = torch.empty(40, dtype=torch.uint8, device=dev)
         modes = {}
+        mws = torch.empty(max(spd.binding.load().spd_msd_workspace_bytes(
+            ctypes.byref(spd.Plane(x, scale=scale).c()), 0, 256), 1), dtype=torch.uint8,
+            device=dev)
         for mode, name in ((1, "eq5_as_printed"), (2, "eq5_linear_excess")):
-            ws = torch.empty(spd.search_workspace_bytes(x, widths, THRESHOLD, mode, 0, 256,
-                                                        scale=scale), dtype=torch.uint8,
-                             device=dev)
-            step = lambda: spd.search(x, widths, THRESHOLD, out.shape[0], mode, 0, 256,
-                                      out=out, result=res, msd_out=msd, workspace=ws, scale=scale)
-            ms, clocks = timed(step, a.steps, a.warmup, 0)
+            dws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+            phases = [lambda: spd.msd(x, 0, 256, out=msd, workspace=mws, scale=scale),
+                      lambda mode=mode: spd.detect(x, msd, widths, THRESHOLD, out.shape[0], mode,
+                                                   0, 256, out=out, result=res, workspace=dws,
+                                                   scale=scale)]
+            ms, (msd_ms, det_ms), clocks = timed_split(phases, a.steps, a.warmup, 0)
             cnt = spd.read_result(res)[0]
             m = spd.msd_to_numpy(msd)[0]
             modes[name] = {"value": n / (ms / 1e3), "ms_per_step": ms, "candidates": cnt,
+                           "step_breakdown_ms": {"msd_and_sigma_nmax": msd_ms, "detect": det_ms},
                            "mean": float(m["mean"]), "sd": float(m["sd"]),
                            "sd_nmax": float(m["sd_nmax"]), "clocks": clocks}
         main_ = modes["eq5_as_printed"]
         in_bytes = n * x.element_size()
+        bd = main_["step_breakdown_ms"]
         line.update(value=main_["value"], ms_per_step=main_["ms_per_step"], dtype=a.dtype,
                     clocks=main_["clocks"], candidates_per_step=main_["candidates"],
                     gpu_launches=8 * a.steps, modes=modes,
+                    roofline=hbm_roofline("search_kernel (boxcar + SNR + max + threshold)",
+                                          in_bytes + 16 * main_["candidates"], bd["detect"],
+                                          recorded_traffic(n, main_["candidates"],
+                                                           f"precision_{a.dtype}")),
+                    msd_roofline=hbm_roofline("MSD (Eq. 1-2) and sigma_Nmax (Eq. 5) passes",
+                                              2 * in_bytes, bd["msd_and_sigma_nmax"],
+                                              note="two reads of the plane"),
                     error_vs_fp64_oracle="tests/test_gpu_precision_error.py (asserted bounds)",
                     realtime_factor=n_samp * SAMPLE_TIME_S / (main_["ms_per_step"] / 1e3),
                     whole_step_hbm_frac=(3 * in_bytes + 16 * main_["candidates"]) /
@@ -540,6 +640,10 @@ def run_other(a):
         line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
                     candidates_per_step=cnt, gpu_launches=(5 * len(specs) + 1) * a.steps,
                     tuning=tune, realtime_factor=dur / (ms / 1e3),
+                    roofline=hbm_roofline("batched step (per-range MSD + one search-kernel "
+                                          "launch), one graph replay", 2 * in_bytes + 16 * cnt,
+                                          ms, note="the graph is timed whole: MSD reads each "
+                                                   "range once more"),
                     whole_step_hbm_frac=(2 * in_bytes + 16 * cnt) / (ms / 1e3) / 1e9 / hbm,
                     config={"workload": "4 DM ranges, decimation 1/2/4/8: 2048x524288, "
                                         "1536x262144, 1024x131072, 512x65536 FP32 N(0,1) + "
@@ -578,6 +682,10 @@ def run_other(a):
                     candidates_per_step=cnt, gpu_launches=(4 + 5 * len(levels)) * a.steps,
                     plain_search={"widths": "1..512", "ms_per_step": ms2, "value": n / (ms2 / 1e3),
                                   "candidates": cnt2},
+                    roofline=hbm_roofline("decimated step (level planes, per-level MSD, one "
+                                          "search launch per level class)",
+                                          2 * 4 * n + 16 * cnt, ms,
+                                          note="algorithmic bytes of the native plane only"),
                     speedup_vs_plain=ms2 / ms,
                     realtime_factor=n_samp * SAMPLE_TIME_S / (ms / 1e3),
                     config={"workload": f"{n_dm} DM x {n_samp} FP32 N(0,1) + 200 Gaussian pulses "
@@ -585,6 +693,63 @@ def run_other(a):
                                         "level samples (native to 512), each level its own "
                                         "MSD; f_T 7",
                             "l2": "inputs larger than L2"})
+        print(json.dumps(line))
+        return 0
+    if a.workload == "plane":
+        n_dm, n_samp = a.n_dm, a.n_samp
+        x = synth.ska_like(n_dm, n_samp, device=dev, seed=1611_1).data
+        n = n_dm * n_samp
+        m = spd.msd(x)
+        snr = torch.empty((n_dm, n_samp), dtype=torch.float32, device=dev)
+        wid = torch.empty((n_dm, n_samp), dtype=torch.int16, device=dev)
+        cap = int(n * 0.45) + 1024
+        out = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+        res = torch.zeros(16, dtype=torch.uint8, device=dev)
+        phases = [lambda: spd.boxcar_snr(x, m, WIDTHS, snr_out=snr, width_out=wid),
+                  lambda: spd.threshold_candidates(snr, wid, THRESHOLD, cap, out=out, result=res)]
+        ms, (box_ms, thr_ms), clocks = timed_split(phases, a.steps, a.warmup, 0)
+        cnt = spd.read_result(res)[0]
+        n_eval = len(WIDTHS) + (WIDTHS[0] != 1)
+        line.update(value=n / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    candidates_per_step=cnt, gpu_launches=3 * a.steps,
+                    step_breakdown_ms={"boxcar_snr": box_ms, "threshold_candidates": thr_ms},
+                    # every width of every sample: add, multiply by 1/sigma_w, max
+                    roofline=alu_roofline("boxcar_snr plane kernel (every width, no pruning)",
+                                          3.0 * n * n_eval + 5.0 * n, box_ms,
+                                          note="3 FP32 operations per (sample, width) + 5 per "
+                                               "sample"),
+                    hbm_roofline_boxcar=hbm_roofline("boxcar_snr plane kernel", 4 * n + 6 * n,
+                                                     box_ms),
+                    threshold_roofline=hbm_roofline("threshold_kernel", 6 * n + 16 * cnt, thr_ms),
+                    config={"workload": f"unfused calls on the SKA-like chunk {n_dm} x {n_samp} "
+                                        "FP32: spd_boxcar_snr (widths 1..16 + 24..256/8) then "
+                                        "spd_threshold_candidates (f_T 7)",
+                            "l2": "inputs larger than L2"})
+        print(json.dumps(line))
+        return 0
+    if a.workload == "dedisperse":
+        n_chan, n_dm = 256, 256
+        dms = np.linspace(0.0, 100.0, n_dm)
+        delays_np = synth.dispersion_delays(n_chan, dms)
+        n_out = 1 << 18
+        fb = synth.filterbank(n_chan, n_out + int(delays_np.max()), dms=dms,
+                              pulses=((100, 5000, 8, 0.5),), device=dev, seed=1611_8)
+        delays = torch.from_numpy(fb.delays).to(dev)
+        plane = torch.empty((n_dm, n_out), dtype=torch.float32, device=dev)
+        step = lambda: spd.dedisperse(fb.data, delays, n_out, out=plane)
+        ms, clocks = timed(step, a.steps, a.warmup, 0)
+        fb_bytes = fb.data.numel() * 4
+        line.update(value=n_dm * n_out / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
+                    gpu_launches=a.steps,
+                    roofline=hbm_roofline("dedisperse_kernel", fb_bytes + n_dm * n_out * 4, ms,
+                                          note="algorithmic bytes: the filterbank read once and "
+                                               "the plane written; the direct sum reads every "
+                                               "channel sample once per DM trial, from L2"),
+                    adds_per_s=n_dm * n_out * n_chan / (ms / 1e3),
+                    config={"workload": f"incoherent de-dispersion, {n_chan} channels "
+                                        f"1200-1500 MHz at 64 us, {n_dm} DM trials 0..100, "
+                                        f"{n_out} output samples, FP32",
+                            "l2": "filterbank %.2f GB" % (fb_bytes / 1e9)})
         print(json.dumps(line))
         return 0
     if a.workload == "cluster":
@@ -673,6 +838,11 @@ def run_serving(a, spd, synth, line, dev):
     n_chunks = sum(len(b.lengths) for b in beams)
     line.update(value=sat["samples_per_s"], ms_per_step=sat["span_s"] * 1e3, dtype="f16",
                 clocks=clocks, steps=1, warmup=max(1, min(a.warmup, 3)),
+                roofline=hbm_roofline("serving pass (H2D + running MSD + search per chunk)",
+                                      2 * 2 * sat["samples"] + 16 * sat["candidates"],
+                                      sat["span_s"] * 1e3,
+                                      note="host-driven pass timed by wall clock: bounded by "
+                                           "the scheduler and host link, not one kernel"),
                 candidates_per_step=sat["candidates"],
                 gpu_launches=n_chunks * 4 + len(beams) * 4,   # push: 4 kernels; reset+flush: 4
                 saturated=dict(sat, max_inflight=inflight_sat),

@@ -328,6 +328,31 @@ spd_status spd_search(const spd_plane *plane, const spd_search_params *params,
                       spd_msd_stats *msd_out_dev, void *workspace, size_t workspace_bytes,
                       void *stream);
 
+/* The whole path for a plane held in HOST memory, the call an application
+ * with a host-side DM x time plane makes.  Blocking: it returns when the
+ * records are in host memory.  The plane (host data and, if given, host
+ * per-row scale / offset) is copied into the workspace, the MSD (a) is
+ * computed there, and the search (b, c, d) runs in blocks of rows.  Each
+ * block's records are copied to host_out on a second stream while the next
+ * block is searched.  Page-locked host memory makes the copies asynchronous;
+ * pageable memory works, with slower synchronous copies.
+ *   host_out: host array of `capacity` records (the first min(count,
+ *     capacity) written, in no stated order); host_result: host summary
+ *     (semantics as spd_search); host_msd: optional host array (1 or n_dm
+ *     entries) receiving the MSD.
+ *   workspace: device, spd_search_host_workspace_bytes(plane, params,
+ *     capacity) bytes, 256-byte aligned; it holds the plane, the records and
+ *     the search's own workspace.
+ * Two host threads may call this at once with their own workspaces and
+ * streams; one plane's copies in then overlap the other's copies out.
+ * Errors: as spd_search, SPD_ERR_CUDA on a failed copy. */
+size_t spd_search_host_workspace_bytes(const spd_plane *plane, const spd_search_params *params,
+                                       int64_t capacity);
+spd_status spd_search_host(const spd_plane *host_plane, const spd_search_params *params,
+                           spd_candidate *host_out, int64_t capacity, spd_result *host_result,
+                           spd_msd_stats *host_msd, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
 /* One DM range of a batched search: a plane with its own search parameters.
  * dm_offset is added to the row index in the range's candidate records, so
  * that ranges can share one record list; decimation records the time

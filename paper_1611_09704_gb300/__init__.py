@@ -12,4 +12,5 @@ from .binding import (  # noqa: F401
     detect, load, msd, msd_to_numpy, read_result, search, search_workspace_bytes,
     threshold_candidates, threshold_plane, widths_to_numpy, RangeSpec, BatchedSearch, search_batched,
     search_batched_workspace_bytes, SpdTuning, BeamStream, search_decimated,
-    search_decimated_workspace_bytes, cluster_rows, clusters_to_numpy, CLUSTER_DTYPE, dedisperse)
+    search_decimated_workspace_bytes, cluster_rows, clusters_to_numpy, CLUSTER_DTYPE, dedisperse,
+    search_host, search_host_workspace_bytes)

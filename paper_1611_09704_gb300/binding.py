@@ -108,7 +108,8 @@ EXPORTS = ["spd_version", "spd_status_string", "spd_last_cuda_error",
            "spd_msd_shard_partial", "spd_msd_merge_partials", "spd_sd_nmax_shard_partial",
            "spd_sd_nmax_merge_partials", "spd_threshold_plane",
            "spd_search_decimated_workspace_bytes", "spd_search_decimated",
-           "spd_debug_set_copy_wait", "spd_cluster_rows", "spd_dedisperse"]
+           "spd_debug_set_copy_wait", "spd_cluster_rows", "spd_dedisperse",
+           "spd_search_host_workspace_bytes", "spd_search_host"]
 
 
 class SpdError(RuntimeError):
@@ -165,6 +166,10 @@ def load(path: str | None = None):
     lib.spd_detect.restype = I32
     lib.spd_search.argtypes = [pp, pq, P, I64, P, P, P, SZ, P]
     lib.spd_search.restype = I32
+    lib.spd_search_host_workspace_bytes.argtypes = [pp, pq, I64]
+    lib.spd_search_host_workspace_bytes.restype = SZ
+    lib.spd_search_host.argtypes = [pp, pq, P, I64, ctypes.POINTER(SpdResult), P, P, SZ, P]
+    lib.spd_search_host.restype = I32
     lib.spd_boxcar_sums.argtypes = [pp, I32, P, I64, P]
     lib.spd_boxcar_sums.restype = I32
     lib.spd_dedisperse.argtypes = [pp, P, I64, P, I32, I64, I64, P, P]
@@ -496,6 +501,33 @@ def debug_set_copy_wait(limit_ns=2_000_000_000, extra_bytes=0):
     run out); the defaults restore normal operation."""
     _check(load().spd_debug_set_copy_wait(int(limit_ns), int(extra_bytes)),
            "spd_debug_set_copy_wait")
+
+
+def search_host_workspace_bytes(x, widths, threshold, capacity, sigma_mode=SIGMA_SQRTN,
+                                scope=MSD_GLOBAL, nmax_sigma=0, **kw) -> int:
+    lib = load()
+    cp = as_plane(x, **kw).c()
+    prm, keep = _params(widths, threshold, sigma_mode, scope, nmax_sigma)
+    return int(lib.spd_search_host_workspace_bytes(ctypes.byref(cp), ctypes.byref(prm),
+                                                   int(capacity)))
+
+
+def search_host(x, widths, threshold, out, sigma_mode=SIGMA_SQRTN, scope=MSD_GLOBAL,
+                nmax_sigma=0, *, workspace, stream=None, msd_out=None, **kw):
+    """spd_search_host: the whole search of a plane in HOST memory (x and its
+    scale / offset on the host, best page-locked); ``out``: host int32
+    [capacity, 4] receiving the records; ``workspace``: device uint8 tensor of
+    search_host_workspace_bytes.  Blocking.  Returns (count, status)."""
+    lib = load()
+    pl = as_plane(x, **kw)
+    cp = pl.c()
+    prm, keep = _params(widths, threshold, sigma_mode, scope, nmax_sigma)
+    res = SpdResult()
+    _check(lib.spd_search_host(ctypes.byref(cp), ctypes.byref(prm), _ptr(out), out.shape[0],
+                               ctypes.byref(res), _ptr(msd_out), _ptr(workspace),
+                               workspace.numel(), _stream(stream)), "spd_search_host")
+    del keep
+    return int(res.count), int(res.status)
 
 
 def dedisperse(fb, delays, n_out, *, out=None, out_dtype=F32, status=None, stream=None, **kw):

@@ -1205,3 +1205,187 @@ spd_status spd_boxcar_sums(const spd_plane *plane, int32_t w, float *out, int64_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- the host-buffer search
+
+namespace {
+
+// Workspace of spd_search_host: the plane (rows padded to 16 bytes), its
+// scale and offset, spd_search's own workspace (MSD part, then the detect
+// constants), the result word, the MSD and the records.
+struct HostLayout {
+    int64_t dstride;
+    size_t plane_off, scale_off, offset_off, search_off, msd_ws_bytes, result_off, msd_off,
+        out_off, total;
+};
+
+spd_status host_layout(const spd_plane *hp, const spd_search_params *q, int64_t capacity,
+                       HostLayout &H) {
+    const size_t eb = elem_bytes(hp->dtype);
+    const int64_t per = (int64_t)(16 / eb);
+    H.dstride = (hp->n_samp + per - 1) / per * per;
+    spd_plane dp = *hp;
+    dp.data = reinterpret_cast<void *>(256);   // any aligned address: sizes only
+    dp.row_stride = H.dstride;
+    const size_t search_bytes = spd_search_workspace_bytes(&dp, q);
+    if (!search_bytes) return SPD_ERR_INVALID_ARG;
+    H.msd_ws_bytes = msd_layout(&dp, nmax_of(q)).total;
+    const int64_t entries = entries_of(hp, q->msd_scope);
+    H.plane_off = 0;
+    H.scale_off = align_up((size_t)hp->n_dm * H.dstride * eb);
+    H.offset_off = H.scale_off + align_up((size_t)hp->n_dm * sizeof(float));
+    H.search_off = H.offset_off + align_up((size_t)hp->n_dm * sizeof(float));
+    H.result_off = H.search_off + align_up(search_bytes);
+    H.msd_off = H.result_off + kAlign;
+    H.out_off = H.msd_off + align_up((size_t)entries * sizeof(spd_msd_stats));
+    H.total = H.out_off + align_up((size_t)capacity * sizeof(spd_candidate));
+    return SPD_OK;
+}
+
+constexpr int kHostBlocks = 16;   // most row blocks of one call
+
+// Per host thread: the copy-out stream and the events of the row blocks (on
+// the device current when they were made), and page-locked result words.
+struct HostAux {
+    int dev = -1;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kHostBlocks] = {};
+    spd_result *pin = nullptr;
+};
+thread_local HostAux g_aux;
+
+cudaError_t host_aux(HostAux **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    HostAux &a = g_aux;
+    if (!a.pin) {
+        e = cudaHostAlloc(reinterpret_cast<void **>(&a.pin), sizeof(spd_result) * kHostBlocks,
+                          cudaHostAllocPortable);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.dev != dev) {
+        e = cudaStreamCreateWithFlags(&a.cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        for (int b = 0; b < kHostBlocks; ++b) {
+            e = cudaEventCreateWithFlags(&a.ev[b], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+        a.dev = dev;
+    }
+    *out = &a;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t spd_search_host_workspace_bytes(const spd_plane *plane, const spd_search_params *params,
+                                       int64_t capacity) {
+    if (check_plane(plane) != SPD_OK || check_params(params) != SPD_OK || capacity < 0) return 0;
+    HostLayout H;
+    if (host_layout(plane, params, capacity, H) != SPD_OK) return 0;
+    return H.total;
+}
+
+spd_status spd_search_host(const spd_plane *host_plane, const spd_search_params *params,
+                           spd_candidate *host_out, int64_t capacity, spd_result *host_result,
+                           spd_msd_stats *host_msd, void *workspace, size_t workspace_bytes,
+                           void *stream) {
+    SPD_TRY(check_plane(host_plane));
+    SPD_TRY(check_params(params));
+    if (!host_result || capacity < 0 || (capacity > 0 && !host_out)) return SPD_ERR_INVALID_ARG;
+    static thread_local RangeProg prog;
+    SPD_TRY(compile_program(params->widths, params->n_widths, prog, 1, true));
+    HostLayout H;
+    SPD_TRY(host_layout(host_plane, params, capacity, H));
+    SPD_TRY(check_ws(workspace, workspace_bytes, H.total));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(workspace);
+    spd_result *res = reinterpret_cast<spd_result *>(base + H.result_off);
+    spd_msd_stats *msd = reinterpret_cast<spd_msd_stats *>(base + H.msd_off);
+    spd_candidate *dev_out = reinterpret_cast<spd_candidate *>(base + H.out_off);
+    const int64_t n_dm = host_plane->n_dm;
+    const size_t eb = elem_bytes(host_plane->dtype);
+    if (plane_empty(host_plane)) {
+        memset(host_result, 0, sizeof(spd_result));
+        return SPD_OK;
+    }
+
+    // the plane and its scale / offset into device memory
+    void *dplane = base + H.plane_off;
+    spd_plane dp = *host_plane;
+    dp.data = dplane;
+    dp.row_stride = H.dstride;
+    SPD_CK(cudaMemcpy2DAsync(dplane, (size_t)H.dstride * eb, host_plane->data,
+                             (size_t)host_plane->row_stride * eb, (size_t)host_plane->n_samp * eb,
+                             (size_t)n_dm, cudaMemcpyHostToDevice, st));
+    if (host_plane->row_scale) {
+        float *sc = reinterpret_cast<float *>(base + H.scale_off);
+        SPD_CK(cudaMemcpyAsync(sc, host_plane->row_scale, n_dm * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+        dp.row_scale = sc;
+    }
+    if (host_plane->row_offset) {
+        float *of = reinterpret_cast<float *>(base + H.offset_off);
+        SPD_CK(cudaMemcpyAsync(of, host_plane->row_offset, n_dm * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+        dp.row_offset = of;
+    }
+
+    // (a) the MSD of the whole plane, the result word zeroed, then the
+    // constants of every row once
+    char *sws = base + H.search_off;
+    SPD_TRY(spd_msd(&dp, params->msd_scope, nmax_of(params), msd, sws, H.msd_ws_bytes, stream));
+    SPD_CK(cudaMemsetAsync(res, 0, sizeof(spd_result), st));
+    RangeDesc rd;
+    SPD_TRY(range_consts(&dp, prog, msd, params->msd_scope, params->sigma_mode, res,
+                         sws + H.msd_ws_bytes, st, rd));
+    rd.threshold = params->threshold;
+
+    // (b, c, d) by blocks of rows; block b's records go out while b + 1 runs
+    HostAux *aux = nullptr;
+    SPD_CK(host_aux(&aux));
+    int nb = (int)(n_dm / 256);
+    nb = nb < 1 ? 1 : (nb > kHostBlocks ? kHostBlocks : nb);
+    for (int b = 0; b < nb; ++b) {
+        const int64_t r0 = n_dm * b / nb, r1 = n_dm * (b + 1) / nb;
+        RangeDesc rb = rd;
+        rb.data = static_cast<const char *>(dp.data) + r0 * H.dstride * (int64_t)eb;
+        rb.n_dm = r1 - r0;
+        if (rb.scale) rb.scale += r0;
+        if (rb.offset) rb.offset += r0;
+        if (rd.per_row) {
+            rb.inv_tab += r0 * prog.n_eval;
+            rb.mu_tab += r0;
+            rb.flags += r0;
+        }
+        rb.dm_offset = (int32_t)r0;
+        SPD_TRY(run_launch(&rb, 1, dp.dtype, dev_out, capacity, res, nullptr, nullptr, 0, 0, st));
+        SPD_CK(cudaMemcpyAsync(aux->pin + b, res, sizeof(spd_result), cudaMemcpyDeviceToHost, st));
+        SPD_CK(cudaEventRecord(aux->ev[b], st));
+    }
+    uint64_t done = 0;
+    for (int b = 0; b < nb; ++b) {
+        SPD_CK(cudaEventSynchronize(aux->ev[b]));
+        const uint64_t c = aux->pin[b].count < (uint64_t)capacity ? aux->pin[b].count
+                                                                 : (uint64_t)capacity;
+        if (c > done) {
+            SPD_CK(cudaStreamWaitEvent(aux->cs, aux->ev[b], 0));
+            SPD_CK(cudaMemcpyAsync(host_out + done, dev_out + done,
+                                   (size_t)(c - done) * sizeof(spd_candidate),
+                                   cudaMemcpyDeviceToHost, aux->cs));
+            done = c;
+        }
+    }
+    if (host_msd)
+        SPD_CK(cudaMemcpyAsync(host_msd, msd,
+                               (size_t)entries_of(&dp, params->msd_scope) * sizeof(spd_msd_stats),
+                               cudaMemcpyDeviceToHost, aux->cs));
+    SPD_CK(cudaStreamSynchronize(aux->cs));
+    *host_result = aux->pin[nb - 1];
+    return SPD_OK;
+}
+
+}  // extern "C"

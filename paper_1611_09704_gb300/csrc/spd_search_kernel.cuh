@@ -504,9 +504,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         // records start index by start index: for start q the lanes holding a
         // candidate there write consecutive slots (rank among them by
         // ballot), so each store instruction is one coalesced run
+        // unsigned: whatever the count word held before, no slot lies
+        // outside out[0, capacity)
         const unsigned long long wb = s_wbase[warp];
-        const long long room = (long long)L.capacity - (long long)wb;
-        const int nroom = room <= 0 ? 0 : (room < pwtot ? (int)room : pwtot);
+        const unsigned long long cap = (unsigned long long)L.capacity;
+        const unsigned long long room = wb >= cap ? 0ull : cap - wb;
+        const int nroom = room < (unsigned long long)pwtot ? (int)room : pwtot;
         int4 *dst = reinterpret_cast<int4 *>(L.out) + wb;
         const uint32_t ltm = (1u << lane) - 1u;
         int off = 0;
