@@ -227,7 +227,7 @@ struct ConstArgs {
     float *inv_tab;
     float2 *mu_tab;
     int32_t *flags;
-    spd_result *result;   // may be null: zeroed count/status when given
+    spd_result *result;   // may be null: status set on a degenerate entry (count untouched)
     int skip_w1;          // eval index 0 (the width-1 start) takes no part: 1/sigma = NaN
 };
 

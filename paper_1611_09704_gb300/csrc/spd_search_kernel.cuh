@@ -485,19 +485,24 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
     constexpr int kAtomicThread = kThreads - 32;   // lane 0 of the last warp
     uint32_t pmask = 0, pbits[kX], pobk[MG ? kX / 4 : 1];
     int pdm = 0, psb = 0, psh = 0, pwtot = 0;
-    auto reserve = [&]() {   // kAtomicThread: slices of the last tile's records
-        int tot = 0, pre[kThreads / 32];
+    // kAtomicThread: one atomic reserves the last tile's records; the warps'
+    // slices are published from its result only after this thread's staging,
+    // so that the round trip of the atomic (L2, possibly on the other die)
+    // overlaps the staging instead of delaying this warp at the next barrier
+    auto reserve = [&]() -> unsigned long long {
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_wsum[w];
+        return tot ? atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
+                               (unsigned long long)tot)
+                   : 0ull;
+    };
+    auto publish = [&](unsigned long long base) {   // s_wsum unchanged since reserve()
 #pragma unroll
         for (int w = 0; w < kThreads / 32; ++w) {
-            pre[w] = tot;
-            tot += s_wsum[w];
+            s_wbase[w] = base;
+            base += (unsigned long long)s_wsum[w];
         }
-        unsigned long long base = 0;
-        if (tot)
-            base = atomicAdd(reinterpret_cast<unsigned long long *>(&L.result->count),
-                             (unsigned long long)tot);
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) s_wbase[w] = base + (unsigned long long)pre[w];
     };
     auto flush = [&]() {     // a warp writes the last tile's records
         if (!pwtot) return;   // warp-uniform
@@ -553,12 +558,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         } else {
             __syncthreads();
         }
-        if (k && tid == kAtomicThread) reserve();
+        bool held = k && tid == kAtomicThread;   // a reservation not yet published
+        unsigned long long rbase = 0;
+        if (held) rbase = reserve();
         {
             const int64_t nk = ((int64_t)ri << 32) | (uint32_t)entry;
             if (nk != key) {
                 // the last tile's records read the widths it was searched with
                 if (k) {
+                    if (held) publish(rbase);
+                    held = false;
                     __syncthreads();
                     flush();
                 }
@@ -571,6 +580,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
             }
         }
         if (s_deg) {   // degenerate sigma: no candidates (uniform across the CTA)
+            if (held) publish(rbase);
             __syncthreads();
             if (tma && tid == 0 && more) issue(advance(pos));
             flush();
@@ -673,6 +683,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
                 s_eq[c] = lane ? eqv : 0.f;
             }
         }
+        if (held) publish(rbase);
         __syncthreads();   // (B)
         // the raw buffer is free: fetch the next tile's window
         if (tma && tid == 0 && more) issue(advance(pos));
@@ -920,7 +931,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
     }
     // the last tile's records
     __syncthreads();
-    if (tid == kAtomicThread) reserve();
+    if (tid == kAtomicThread) publish(reserve());
     __syncthreads();
     flush();
 }
