@@ -166,6 +166,22 @@ def alu_roofline(kernel: str, ops: float, ms: float, note=None):
     return r
 
 
+def lds_roofline(kernel: str, words: float, ms: float, note=None):
+    """Roofline object of a kernel bound by shared-memory reads (one 32-bit
+    word per arithmetic operation): words over the CUDA-event time, against
+    SMs x 32 words per clock x the measured maximum SM clock."""
+    mhz = sm_max_mhz()
+    peak = SM_COUNT * 32 * mhz * 1e6 / 1e12
+    ach = words / (ms / 1e3) / 1e12
+    r = {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "Twords/s",
+         "frac": ach / peak, "traffic": None,
+         "peak_source": f"{SM_COUNT} SMs x 32 shared-memory words/clk x {mhz:.0f} MHz",
+         "algorithmic_words": words, "ms": ms}
+    if note:
+        r["note"] = note
+    return r
+
+
 SM_COUNT, SCHEDULERS_PER_SM = 152, 4
 
 
@@ -381,6 +397,14 @@ def run_spd(a, rank, world, local):
     e2e_line = None
     if not a.no_e2e:
         e2e_line = e2e(x, count, a.e2e_steps, n, world, rank, dev)
+        link = host_link(dev)
+        hb, db = e2e_line["h2d_bytes_per_step"], e2e_line["d2h_bytes_per_step"]
+        # lower bound of a plane's time from the link alone: neither direction
+        # faster than alone, both together no faster than the duplex aggregate
+        link["bound_ms_per_step"] = 1e3 * max(
+            hb / (link["h2d_gbs"] * 1e9), db / (link["d2h_gbs"] * 1e9),
+            (hb + db) / (2 * link["duplex_gbs_each"] * 1e9))
+        e2e_line["host_link"] = link
     if rank != 0:
         return 0
 
@@ -412,6 +436,44 @@ def run_spd(a, rank, world, local):
                                           f"oracle MSD over the sample, {dt:.1f} s"}
     print(json.dumps(line))
     return 0
+
+
+def host_link(dev, nbytes=1 << 30, reps=3):
+    """Page-locked host <-> device copy rates (GB/s) of this GPU's host link:
+    each direction alone and both at once on two streams, CUDA-event timed."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def rate(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return reps * nbytes / (time.perf_counter() - t0) / 1e9
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+
+    # both(): nbytes each way per repetition, so its rate is per direction
+    r = {"h2d_gbs": rate(h2d), "d2h_gbs": rate(d2h), "duplex_gbs_each": rate(both)}
+    del h, h2, d, d2
+    torch.cuda.empty_cache()
+    return r
 
 
 def e2e(x, count, steps, n, world, rank, dev):
@@ -741,10 +803,13 @@ def run_other(a):
         fb_bytes = fb.data.numel() * 4
         line.update(value=n_dm * n_out / (ms / 1e3), ms_per_step=ms, dtype="f32", clocks=clocks,
                     gpu_launches=a.steps,
-                    roofline=hbm_roofline("dedisperse_kernel", fb_bytes + n_dm * n_out * 4, ms,
-                                          note="algorithmic bytes: the filterbank read once and "
-                                               "the plane written; the direct sum reads every "
-                                               "channel sample once per DM trial, from L2"),
+                    roofline=lds_roofline("dedisperse_kernel", float(n_dm) * n_out * n_chan, ms,
+                                          note="one FP32 add per (DM trial, channel, sample), "
+                                               "its operand read from the channel window "
+                                               "staged in shared memory"),
+                    hbm_roofline=hbm_roofline("dedisperse_kernel", fb_bytes + n_dm * n_out * 4,
+                                              ms, note="the filterbank read once and the plane "
+                                                       "written"),
                     adds_per_s=n_dm * n_out * n_chan / (ms / 1e3),
                     config={"workload": f"incoherent de-dispersion, {n_chan} channels "
                                         f"1200-1500 MHz at 64 us, {n_dm} DM trials 0..100, "

@@ -15,8 +15,13 @@ using namespace spd;
 namespace {
 
 constexpr int kDdThreads = 256;
-constexpr int kDdPer = 4;                      // outputs per thread
-constexpr int kDdSpan = kDdThreads * kDdPer;   // outputs per CTA
+constexpr int kDdPer = 2;                        // outputs per thread and DM trial
+constexpr int kDdSpan = kDdThreads * kDdPer;     // output samples per CTA
+constexpr int kDdDms = 16;                       // DM trials per CTA
+constexpr int kDdChunk = 128;                    // channels whose delays are staged at once
+constexpr int kDdSpread = 1536;                  // delay spread of a DM block held in shared memory
+constexpr int kDdWin = kDdSpan + kDdSpread;      // staged window of one channel
+constexpr int kDdLoads = kDdWin / kDdThreads;    // staging loads per thread
 
 template <int DT>
 __device__ __forceinline__ float fb_value(const typename Elem<DT>::T *p, bool has_sc, float sc,
@@ -31,47 +36,144 @@ __device__ __forceinline__ void store_out(void *out, int dt, int64_t idx, float 
     else static_cast<__nv_bfloat16 *>(out)[idx] = __float2bfloat16_rn(v);
 }
 
-// One CTA: kDdSpan consecutive outputs of one DM trial (grid.y walks the DM
-// trials).  Thread t sums outputs t0 + t + 256 j, j < 4: at every channel the
-// warp reads consecutive samples, and the channel's delay is one broadcast.
+// One CTA: kDdSpan consecutive outputs t0 .. of kDdDms consecutive DM trials
+// d0 ...  For every channel c the trials of the block read the one window
+// x[c][t0 + lo_c, t0 + kDdSpan + hi_c) (lo_c, hi_c: the smallest and largest
+// delay of the block at c), which is staged in shared memory by coalesced
+// loads (double-buffered, the next channel's loads in flight while the
+// current one is summed); thread t sums outputs t0 + t + 256 j, j < 2, of
+// every trial from it.  Channels are summed in order c = 0, 1, ... for every
+// output.  A block whose spread at some channel exceeds kDdSpread reads that
+// channel from global memory instead.  A delay outside [0, n_samp - n_out]
+// makes its trial's outputs NaN and sets the status (no read outside the row).
 template <int DT>
 __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
     const typename Elem<DT>::T *fb, int64_t n_chan, int64_t n_samp, int64_t fb_stride,
     const float *scale, const float *offset, const int32_t *delays, int64_t n_dm, void *out,
     int out_dt, int64_t n_out, int64_t out_stride, spd_result *status) {
     using T = typename Elem<DT>::T;
-    const int64_t t0 = (int64_t)blockIdx.x * kDdSpan + threadIdx.x;
+    __shared__ float s_x[2][kDdWin];
+    __shared__ int32_t s_dl[kDdChunk][kDdDms];
+    __shared__ int32_t s_lo[kDdChunk], s_hi[kDdChunk];
+    __shared__ uint32_t s_bad;                   // bit d: trial d0 + d has a bad delay
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * kDdSpan;
     const int64_t max_delay = n_samp - n_out;
     const bool has_sc = scale != nullptr;
-    for (int64_t d = blockIdx.y; d < n_dm; d += gridDim.y) {
-        const int32_t *dl = delays + d * n_chan;
-        float acc[kDdPer];
+    for (int64_t d0 = (int64_t)blockIdx.y * kDdDms; d0 < n_dm; d0 += (int64_t)gridDim.y * kDdDms) {
+        const int nd = (int)min((int64_t)kDdDms, n_dm - d0);
+        float acc[kDdDms][kDdPer];
 #pragma unroll
-        for (int j = 0; j < kDdPer; ++j) acc[j] = 0.f;
-        bool bad = false;
-        for (int64_t c = 0; c < n_chan; ++c) {
-            const int64_t dc = __ldg(dl + c);
-            if (dc < 0 || dc > max_delay) {   // no read outside the row
-                bad = true;
+        for (int d = 0; d < kDdDms; ++d)
 #pragma unroll
-                for (int j = 0; j < kDdPer; ++j) acc[j] = __int_as_float(0x7fc00000);
-                continue;
+            for (int j = 0; j < kDdPer; ++j) acc[d][j] = 0.f;
+        if (tid == 0) s_bad = 0u;
+        for (int64_t c0 = 0; c0 < n_chan; c0 += kDdChunk) {
+            const int nc = (int)min((int64_t)kDdChunk, n_chan - c0);
+            __syncthreads();   // the last chunk's delays and windows are no longer read
+            // the chunk's delays; a bad one is replaced by the smallest good
+            // delay of its channel (its trial's result is NaN anyway)
+            for (int i = tid; i < nc * kDdDms; i += kDdThreads) {
+                const int c = i / kDdDms, d = i - c * kDdDms;
+                int32_t v = 0;
+                if (d < nd) {
+                    v = __ldg(delays + (d0 + d) * n_chan + c0 + c);
+                    if (v < 0 || (int64_t)v > max_delay) {
+                        atomicOr(&s_bad, 1u << d);
+                        v = -1;
+                    }
+                }
+                s_dl[c][d] = d < nd ? v : -1;
             }
-            const float sc = has_sc ? __ldg(scale + c) : 1.f;
-            const float of = (has_sc && offset) ? __ldg(offset + c) : 0.f;
-            const T *row = fb + c * fb_stride + dc;
+            __syncthreads();
+            for (int c = tid; c < nc; c += kDdThreads) {
+                int lo = INT32_MAX, hi = -1;
+                for (int d = 0; d < nd; ++d) {
+                    const int v = s_dl[c][d];
+                    if (v >= 0) {
+                        lo = min(lo, v);
+                        hi = max(hi, v);
+                    }
+                }
+                if (hi < 0) lo = hi = 0;
+                for (int d = 0; d < nd; ++d)
+                    if (s_dl[c][d] < 0) s_dl[c][d] = lo;
+                s_lo[c] = lo;
+                s_hi[c] = hi;
+            }
+            __syncthreads();
+            // staging of channel c into buffer b: positions t0 + lo_c + i
+            float pre[kDdLoads];
+            auto fetch = [&](int c) {
+                const int64_t base = t0 + s_lo[c];
+                const T *row = fb + (c0 + c) * fb_stride;
+                const float sc = has_sc ? __ldg(scale + c0 + c) : 1.f;
+                const float of = (has_sc && offset) ? __ldg(offset + c0 + c) : 0.f;
+                const int need = kDdSpan + s_hi[c] - s_lo[c];
 #pragma unroll
-            for (int j = 0; j < kDdPer; ++j) {
-                const int64_t t = t0 + (int64_t)kDdThreads * j;
-                if (t < n_out) acc[j] = __fadd_rn(acc[j], fb_value<DT>(row + t, has_sc, sc, of));
+                for (int u = 0; u < kDdLoads; ++u) {
+                    const int i = tid + u * kDdThreads;
+                    const int64_t q = base + i;
+                    pre[u] = (i < need && q < n_samp) ? fb_value<DT>(row + q, has_sc, sc, of) : 0.f;
+                }
+            };
+            auto put = [&](int b) {
+#pragma unroll
+                for (int u = 0; u < kDdLoads; ++u) s_x[b][tid + u * kDdThreads] = pre[u];
+            };
+            fetch(0);
+            put(0);
+            for (int c = 0; c < nc; ++c) {
+                const int b = c & 1;
+                const bool next = c + 1 < nc;
+                if (next) fetch(c + 1);   // in flight while channel c is summed
+                __syncthreads();          // window c staged; window c - 1 no longer read
+                const int lo = s_lo[c];
+                if (s_hi[c] - lo <= kDdSpread) {
+                    const float *w = s_x[b];
+#pragma unroll
+                    for (int d = 0; d < kDdDms; ++d) {
+                        if (d < nd) {
+                            const int dl = s_dl[c][d] - lo;
+#pragma unroll
+                            for (int j = 0; j < kDdPer; ++j)
+                                acc[d][j] = __fadd_rn(acc[d][j], w[tid + j * kDdThreads + dl]);
+                        }
+                    }
+                } else {   // a wide spread: this channel straight from global memory
+                    const T *row = fb + (c0 + c) * fb_stride;
+                    const float sc = has_sc ? __ldg(scale + c0 + c) : 1.f;
+                    const float of = (has_sc && offset) ? __ldg(offset + c0 + c) : 0.f;
+                    for (int d = 0; d < nd; ++d) {
+                        const int64_t dl = s_dl[c][d];
+#pragma unroll
+                        for (int j = 0; j < kDdPer; ++j) {
+                            const int64_t t = t0 + tid + j * kDdThreads;
+                            if (t < n_out)
+                                acc[d][j] = __fadd_rn(acc[d][j],
+                                                      fb_value<DT>(row + t + dl, has_sc, sc, of));
+                        }
+                    }
+                }
+                if (next) put(b ^ 1);
             }
         }
-        if (bad && status && threadIdx.x == 0 && blockIdx.x == 0)
+        __syncthreads();
+        const uint32_t bad = s_bad;
+        __syncthreads();   // read by all before the next DM block resets it
+        if (bad && status && tid == 0 && blockIdx.x == 0)
             atomicExch(&status->status, (int)SPD_ERR_INVALID_ARG);
 #pragma unroll
-        for (int j = 0; j < kDdPer; ++j) {
-            const int64_t t = t0 + (int64_t)kDdThreads * j;
-            if (t < n_out) store_out(out, out_dt, d * out_stride + t, acc[j]);
+        for (int d = 0; d < kDdDms; ++d) {
+            if (d >= nd) break;
+            const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+            for (int j = 0; j < kDdPer; ++j) {
+                const int64_t t = t0 + tid + j * kDdThreads;
+                if (t < n_out)
+                    store_out(out, out_dt, (d0 + d) * out_stride + t,
+                              ((bad >> d) & 1u) ? nan : acc[d][j]);
+            }
         }
     }
 }
@@ -97,7 +199,8 @@ extern "C" spd_status spd_dedisperse(const spd_plane *fb, const int32_t *delays,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t gx = (n_out + kDdSpan - 1) / kDdSpan;
     if (gx > INT32_MAX) return SPD_ERR_INVALID_ARG;
-    const dim3 grid((unsigned)gx, (unsigned)(n_dm < 65535 ? n_dm : 65535));
+    const int64_t gy = (n_dm + kDdDms - 1) / kDdDms;
+    const dim3 grid((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535));
     switch (fb->dtype) {
         case SPD_F32:
             dedisperse_kernel<SPD_F32><<<grid, kDdThreads, 0, st>>>(

@@ -31,9 +31,12 @@ def spd():
     ("f32", "f16", 33, 5001),     # ragged sizes, FP16 output
     ("f16", "f32", 48, 7000),     # FP16 channels with per-channel scale
     ("bf16", "bf16", 16, 3000),
+    ("f32", "f32", 300, 6000),    # three chunks of channel delays, ragged
 ])
 def test_dedisperse_matches_oracle(spd, in_dt, out_dt, n_chan, n_samp):
-    fb = synth.filterbank(n_chan, n_samp, dms=np.linspace(0, 25, 11),
+    # 11 trials: one partial block of DM trials; 300 channels: 40 trials
+    n_trials = 40 if n_chan > 128 else 11
+    fb = synth.filterbank(n_chan, n_samp, dms=np.linspace(0, 25, n_trials),
                           pulses=((3, 500, 4, 2.0), (9, 900, 16, 1.0)), device=DEV, seed=7)
     x, scale, dt = fb.data, None, "f32"
     if in_dt != "f32":
@@ -53,6 +56,22 @@ def test_dedisperse_matches_oracle(spd, in_dt, out_dt, n_chan, n_samp):
     out_rel = {"f32": 0.0, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}[out_dt]
     tol = 2e-7 * n_chan * mag + out_rel * np.abs(want) + 1e-30
     assert np.all(np.abs(got - want) <= tol), np.abs(got - want).max()
+
+
+def test_wide_delay_spread_matches_oracle(spd):
+    """DM trials far apart (spreads of thousands of samples inside one block
+    of trials): those channels are summed from global memory, the others
+    from the staged window; the same sums either way."""
+    dms = np.concatenate([np.linspace(0, 800, 9), np.linspace(2, 6, 9)])
+    fb = synth.filterbank(24, 21000, dms=dms, pulses=((4, 600, 8, 2.0),), device=DEV, seed=12)
+    assert int(fb.delays.max()) - int(fb.delays.min()) > 1536
+    out = spd.dedisperse(fb.data, torch.from_numpy(fb.delays).to(DEV), fb.n_out)
+    got = out.cpu().numpy().astype(np.float64)
+    op = oracle.Plane(synth.to_host_numpy(fb.data))
+    want = oracle.dedisperse(op, fb.delays, fb.n_out)
+    mag = oracle.dedisperse(oracle.Plane(np.abs(op.values()).astype(np.float32)), fb.delays,
+                            fb.n_out)
+    assert np.all(np.abs(got - want) <= 2e-7 * 24 * mag + 1e-30)
 
 
 def test_out_of_range_delay_sets_status(spd):
