@@ -18,10 +18,11 @@ constexpr int kDdThreads = 256;
 constexpr int kDdPer = 2;                        // outputs per thread and DM trial
 constexpr int kDdSpan = kDdThreads * kDdPer;     // output samples per CTA
 constexpr int kDdDms = 16;                       // DM trials per CTA
-constexpr int kDdChunk = 128;                    // channels whose delays are staged at once
-constexpr int kDdSpread = 1536;                  // delay spread of a DM block held in shared memory
+constexpr int kDdChunk = 256;                    // channels whose delays are staged at once
+constexpr int kDdSpread = 1024;                  // delay spread of a DM block held in shared memory
 constexpr int kDdWin = kDdSpan + kDdSpread;      // staged window of one channel
-constexpr int kDdLoads = kDdWin / kDdThreads;    // staging loads per thread
+constexpr int kDdLoads = kDdWin / kDdThreads;    // staging loads per thread (register path)
+constexpr int kDdRing = 4;                       // channel windows in flight (FP32)
 
 template <int DT>
 __device__ __forceinline__ float fb_value(const typename Elem<DT>::T *p, bool has_sc, float sc,
@@ -36,23 +37,41 @@ __device__ __forceinline__ void store_out(void *out, int dt, int64_t idx, float 
     else static_cast<__nv_bfloat16 *>(out)[idx] = __float2bfloat16_rn(v);
 }
 
+// 4-byte asynchronous copy global -> shared; with valid false nothing is read
+// and the word is zero-filled.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // One CTA: kDdSpan consecutive outputs t0 .. of kDdDms consecutive DM trials
 // d0 ...  For every channel c the trials of the block read the one window
 // x[c][t0 + lo_c, t0 + kDdSpan + hi_c) (lo_c, hi_c: the smallest and largest
-// delay of the block at c), which is staged in shared memory by coalesced
-// loads (double-buffered, the next channel's loads in flight while the
-// current one is summed); thread t sums outputs t0 + t + 256 j, j < 2, of
-// every trial from it.  Channels are summed in order c = 0, 1, ... for every
-// output.  A block whose spread at some channel exceeds kDdSpread reads that
-// channel from global memory instead.  A delay outside [0, n_samp - n_out]
-// makes its trial's outputs NaN and sets the status (no read outside the row).
+// delay of the block at c), staged in shared memory; thread t sums outputs
+// t0 + t + 256 j, j < 2, of every trial from it.  FP32 rows arrive by
+// asynchronous copies kDdRing - 1 channels ahead of the channel being summed
+// (a ring of windows, one barrier per channel); FP16 / BF16 rows are loaded
+// one channel ahead into registers, decoded and stored (double buffer).
+// Channels are summed in order c = 0, 1, ... for every output.  A block whose
+// spread at some channel exceeds kDdSpread reads that channel from global
+// memory instead.  A delay outside [0, n_samp - n_out] makes its trial's
+// outputs NaN and sets the status (no read outside the row).
 template <int DT>
 __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
     const typename Elem<DT>::T *fb, int64_t n_chan, int64_t n_samp, int64_t fb_stride,
     const float *scale, const float *offset, const int32_t *delays, int64_t n_dm, void *out,
     int out_dt, int64_t n_out, int64_t out_stride, spd_result *status) {
     using T = typename Elem<DT>::T;
-    __shared__ float s_x[2][kDdWin];
+    __shared__ __align__(16) float s_x[kDdRing][kDdWin];
     __shared__ int32_t s_dl[kDdChunk][kDdDms];
     __shared__ int32_t s_lo[kDdChunk], s_hi[kDdChunk];
     __shared__ uint32_t s_bad;                   // bit d: trial d0 + d has a bad delay
@@ -102,35 +121,10 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                 s_hi[c] = hi;
             }
             __syncthreads();
-            // staging of channel c into buffer b: positions t0 + lo_c + i
-            float pre[kDdLoads];
-            auto fetch = [&](int c) {
-                const int64_t base = t0 + s_lo[c];
-                const T *row = fb + (c0 + c) * fb_stride;
-                const float sc = has_sc ? __ldg(scale + c0 + c) : 1.f;
-                const float of = (has_sc && offset) ? __ldg(offset + c0 + c) : 0.f;
-                const int need = kDdSpan + s_hi[c] - s_lo[c];
-#pragma unroll
-                for (int u = 0; u < kDdLoads; ++u) {
-                    const int i = tid + u * kDdThreads;
-                    const int64_t q = base + i;
-                    pre[u] = (i < need && q < n_samp) ? fb_value<DT>(row + q, has_sc, sc, of) : 0.f;
-                }
-            };
-            auto put = [&](int b) {
-#pragma unroll
-                for (int u = 0; u < kDdLoads; ++u) s_x[b][tid + u * kDdThreads] = pre[u];
-            };
-            fetch(0);
-            put(0);
-            for (int c = 0; c < nc; ++c) {
-                const int b = c & 1;
-                const bool next = c + 1 < nc;
-                if (next) fetch(c + 1);   // in flight while channel c is summed
-                __syncthreads();          // window c staged; window c - 1 no longer read
+            // channel c into the accumulators, from its staged window w
+            auto sum_channel = [&](int c, const float *w) {
                 const int lo = s_lo[c];
                 if (s_hi[c] - lo <= kDdSpread) {
-                    const float *w = s_x[b];
 #pragma unroll
                     for (int d = 0; d < kDdDms; ++d) {
                         if (d < nd) {
@@ -144,7 +138,9 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                     const T *row = fb + (c0 + c) * fb_stride;
                     const float sc = has_sc ? __ldg(scale + c0 + c) : 1.f;
                     const float of = (has_sc && offset) ? __ldg(offset + c0 + c) : 0.f;
-                    for (int d = 0; d < nd; ++d) {
+#pragma unroll
+                    for (int d = 0; d < kDdDms; ++d) {
+                        if (d >= nd) break;
                         const int64_t dl = s_dl[c][d];
 #pragma unroll
                         for (int j = 0; j < kDdPer; ++j) {
@@ -155,7 +151,67 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                         }
                     }
                 }
-                if (next) put(b ^ 1);
+            };
+            // positions of channel c's window that are staged (none for a
+            // channel read from global memory)
+            auto need_of = [&](int c) {
+                const int sp = s_hi[c] - s_lo[c];
+                return sp <= kDdSpread ? kDdSpan + sp : 0;
+            };
+            if constexpr (DT == SPD_F32) {
+                auto stage = [&](int c) {   // one copy group per channel, empty ones too
+                    if (c < nc) {
+                        const int64_t base = t0 + s_lo[c];
+                        const float *row = reinterpret_cast<const float *>(fb) + (c0 + c) * fb_stride;
+                        const int need = need_of(c);
+                        float *w = s_x[c % kDdRing];
+                        for (int i = tid; i < need; i += kDdThreads) {
+                            const int64_t q = base + i;
+                            const bool ok = q < n_samp;   // past the row end: zeros, never read
+                            cp_async4(w + i, ok ? row + q : row, ok);
+                        }
+                    }
+                    cp_async_commit();
+                };
+#pragma unroll
+                for (int c = 0; c < kDdRing - 1; ++c) stage(c);
+                for (int c = 0; c < nc; ++c) {
+                    cp_async_wait<kDdRing - 2>();   // this thread's copies of channel c landed
+                    __syncthreads();                // everyone's; channel c - 1 is summed
+                    stage(c + kDdRing - 1);         // into the slot channel c - 1 used
+                    sum_channel(c, s_x[c % kDdRing]);
+                }
+                cp_async_wait<0>();
+            } else {
+                float pre[kDdLoads];
+                auto fetch = [&](int c) {
+                    const int64_t base = t0 + s_lo[c];
+                    const T *row = fb + (c0 + c) * fb_stride;
+                    const float sc = has_sc ? __ldg(scale + c0 + c) : 1.f;
+                    const float of = (has_sc && offset) ? __ldg(offset + c0 + c) : 0.f;
+                    const int need = need_of(c);
+#pragma unroll
+                    for (int u = 0; u < kDdLoads; ++u) {
+                        const int i = tid + u * kDdThreads;
+                        const int64_t q = base + i;
+                        pre[u] = (i < need && q < n_samp) ? fb_value<DT>(row + q, has_sc, sc, of)
+                                                          : 0.f;
+                    }
+                };
+                auto put = [&](int b) {
+#pragma unroll
+                    for (int u = 0; u < kDdLoads; ++u) s_x[b][tid + u * kDdThreads] = pre[u];
+                };
+                fetch(0);
+                put(0);
+                for (int c = 0; c < nc; ++c) {
+                    const int b = c & 1;
+                    const bool next = c + 1 < nc;
+                    if (next) fetch(c + 1);   // in flight while channel c is summed
+                    __syncthreads();          // window c staged; window c - 1 no longer read
+                    sum_channel(c, s_x[b]);
+                    if (next) put(b ^ 1);
+                }
             }
         }
         __syncthreads();
