@@ -134,7 +134,10 @@ typedef struct {
  * SNR >= threshold; for spd_cluster_rows the number of clusters.
  * status: SPD_OK, SPD_ERR_DEGENERATE_SIGMA, or SPD_ERR_TIMEOUT (a tile's bulk
  * copy did not land within the kernel's wait bound, 2 s: the kernel stopped
- * instead of waiting on; see spd_debug_set_copy_wait). */
+ * instead of waiting on; see spd_debug_set_copy_wait).
+ * reserved0: the candidate search's work counter while its kernels run (the
+ * calls zero the whole word first); 0 again once they have finished, unless
+ * one stopped on SPD_ERR_TIMEOUT. */
 typedef struct {
     uint64_t count;
     int32_t status;

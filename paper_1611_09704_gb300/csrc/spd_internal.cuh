@@ -147,7 +147,7 @@ struct Launch {
     uint32_t extra_tx;          // test aid: bytes expected beyond each copy (0 in use)
     int32_t kmax;               // search kernel: levels of the block max table
     int32_t units;              // search kernel: units of 16 starts per tile (<= threads)
-    int32_t reserved1;
+    int32_t chunk;              // search kernel: tiles per scheduling chunk (set at launch)
     RangeDesc rng[kMaxRanges];
 };
 

@@ -426,11 +426,34 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t esz = (int64_t)sizeof(T);
-    // a contiguous run of the launch's tiles per CTA (consecutive tiles of a
-    // row: the next window's start is this window's halo, still in L2)
-    const int64_t T0 = (int64_t)blockIdx.x * L.n_tiles / gridDim.x;
-    const int64_t T1 = (int64_t)(blockIdx.x + 1) * L.n_tiles / gridDim.x;
-    if (T0 >= T1) return;
+    // Tiles go in chunks of L.chunk consecutive tiles.  CTA b starts with
+    // chunk b, then takes chunk gridDim.x + v for v from an atomic counter,
+    // claimed one chunk ahead of need: CTAs that meet costly tiles (wide
+    // width lists, dense candidates) take fewer of them.  The chunks in
+    // flight at one time are neighbours, so a window's halo is still in L2.
+    // The counter (the result word's reserved field) is 0 at launch; the CTA
+    // that gets the last claim of all sets it back to 0.
+    auto counter = [&]() { return reinterpret_cast<unsigned *>(&L.result->reserved0); };
+    int64_t tile = (int64_t)blockIdx.x * L.chunk;   // the host launches at most n_chunks CTAs
+    // the launch's tile count and chunk length, read from shared memory where
+    // needed (kept out of registers through the search)
+    __shared__ long long s_ntiles;
+    __shared__ int s_chunk;
+    if (tid == 0) {
+        s_ntiles = L.n_tiles;
+        s_chunk = L.chunk;
+    }
+    __syncthreads();
+    // chunks are aligned and a power of two long: a tile is its chunk's last
+    // when the next one starts a chunk
+    auto chunk_ends = [&]() {
+        return (((uint32_t)tile + 1u) & (uint32_t)(s_chunk - 1)) == 0u || tile + 1 == s_ntiles;
+    };
+    __shared__ long long s_next;                // first tile of the next chunk, or -1
+    __shared__ unsigned s_claim;                // thread 0's claim for the chunk after this one
+    unsigned claim = 0;                         // thread 0, until it parks it in s_claim
+    bool claimed = tid == 0;
+    if (claimed) claim = atomicAdd(counter(), 1u);
 
     const bool tma = L.rng[0].vec_ok != 0;   // all ranges of a launch agree (the host checks)
     if (tma) {
@@ -440,15 +463,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         }
         __syncthreads();
     }
-    TilePos pos;
-    {
+    auto pos_of = [&](int64_t t) {
+        TilePos p;
         int r = 0;
-        while (r + 1 < L.n_ranges && T0 >= L.rng[r + 1].tile0) ++r;
-        const int64_t lt = T0 - L.rng[r].tile0;
-        pos.ri = r;
-        pos.row = lt / L.rng[r].tiles_per_row;
-        pos.col = lt - pos.row * L.rng[r].tiles_per_row;
-    }
+        while (r + 1 < L.n_ranges && t >= L.rng[r + 1].tile0) ++r;
+        const int64_t lt = t - L.rng[r].tile0;
+        p.ri = r;
+        p.row = lt / L.rng[r].tiles_per_row;
+        p.col = lt - p.row * L.rng[r].tiles_per_row;
+        return p;
+    };
+    TilePos pos = pos_of(tile);
     auto advance = [&](TilePos p) {
         if (++p.col == L.rng[p.ri].tiles_per_row) {
             p.col = 0;
@@ -473,6 +498,23 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         }
     };
     if (tma && tid == 0) issue(pos);
+    // thread 0, once the current window is staged: the next tile's window into
+    // the raw buffer, and at a chunk's last tile the next chunk for everyone
+    auto issue_next = [&]() {
+        int64_t nt = -1;
+        if (!chunk_ends()) {
+            nt = tile + 1;
+        } else {
+            const unsigned v = s_claim;
+            const int64_t ch = s_chunk;
+            const int64_t n_chunks = (s_ntiles + ch - 1) / ch;
+            const int64_t nc = (int64_t)gridDim.x + (int64_t)v;
+            if (nc < n_chunks) nt = nc * ch;
+            else if ((int64_t)v == n_chunks - 1) atomicExch(counter(), 0u);   // the last claim
+            s_next = nt;
+        }
+        if (tma && nt >= 0) issue(nt == tile + 1 ? advance(pos) : pos_of(nt));
+    };
 
     int64_t key = -1;                       // (range, scope entry) of the constants loaded
     int64_t skey = -1;                      // (range, row) whose scale and offset are held
@@ -533,8 +575,20 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         }
         pwtot = 0;
     };
-    for (int64_t tile = T0, k = 0; tile < T1; ++tile, ++k) {
-        if (k) pos = advance(pos);
+    for (int64_t k = 0;; ++k) {
+        if (k) {   // the next tile: within the chunk, else the next chunk's first
+            if (!chunk_ends()) {
+                ++tile;
+                pos = advance(pos);
+            } else {
+                const int64_t nt = s_next;   // written before the last barrier
+                if (nt < 0) break;
+                tile = nt;
+                pos = pos_of(tile);
+                claimed = tid == 0;
+                if (claimed) claim = atomicAdd(counter(), 1u);
+            }
+        }
         const int ri = pos.ri;
         const RangeDesc &rd = L.rng[ri];
         const RangeProg &rp = rd.prog;
@@ -543,7 +597,6 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         const int64_t t0 = pos.col * (int64_t)kTile;
         const int entry = rd.per_row ? (int)row : 0;
         const T *rowp = static_cast<const T *>(rd.data) + row * rd.stride + t0;
-        const bool more = tile + 1 < T1;
 
         // (A) the window has landed; every thread is done with the last tile
         if (tma) {
@@ -582,7 +635,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         if (s_deg) {   // degenerate sigma: no candidates (uniform across the CTA)
             if (held) publish(rbase);
             __syncthreads();
-            if (tma && tid == 0 && more) issue(advance(pos));
+            if (claimed) s_claim = claim;
+            claimed = false;
+            if (tid == 0) issue_next();
             flush();
             __syncthreads();   // every warp has read its slice before the counts change
             if (lane == 0) s_wsum[warp] = 0;
@@ -684,9 +739,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
             }
         }
         if (held) publish(rbase);
+        if (claimed) s_claim = claim;   // the atomic's round trip overlapped the staging
+        claimed = false;
         __syncthreads();   // (B)
         // the raw buffer is free: fetch the next tile's window
-        if (tma && tid == 0 && more) issue(advance(pos));
+        if (tid == 0) issue_next();
         flush();           // the last tile's records, into the slice reserved above
 
         // ---- prefix values at block starts, their maxima, energy prefix
@@ -950,8 +1007,16 @@ cudaError_t launch_sgn(const Launch &L, bool mg, size_t smem, int ctas_per_sm, c
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-    const int64_t grid = L.n_tiles < (int64_t)sms * per_sm ? L.n_tiles : (int64_t)sms * per_sm;
-    k<<<(unsigned)grid, NT, smem, s>>>(L);
+    // chunks of 1 to 16 tiles (a power of two), about 8 per CTA at least
+    const int64_t gmax = (int64_t)sms * per_sm;
+    int64_t ch = 16;
+    while (ch > 1 && L.n_tiles < 8 * gmax * ch) ch >>= 1;
+    Launch Lc = L;
+    Lc.chunk = (int32_t)ch;
+    const int64_t n_chunks = (L.n_tiles + ch - 1) / ch;
+    const int64_t grid = n_chunks < gmax ? n_chunks : gmax;
+    if (grid < 1) return cudaSuccess;
+    k<<<(unsigned)grid, NT, smem, s>>>(Lc);
     return cudaGetLastError();
 }
 

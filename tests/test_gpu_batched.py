@@ -108,6 +108,9 @@ def test_batched_mixed_storage_types(spd):
     out, res, _ = spd.search_batched(specs, 1_000_000)
     c, st = spd.read_result(res)
     assert st == 0 and c == want.size and c > 0
+    # three launches shared the result word: the search's work counter in it
+    # is back at 0 after each
+    assert res.cpu()[12:16].view(torch.int32).item() == 0
     got = _key(spd.candidates_to_numpy(out, c))
     _oracle_check(spd, specs, got, 1_000_000)
     assert np.array_equal(got, want)
