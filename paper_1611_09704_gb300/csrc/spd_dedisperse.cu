@@ -76,10 +76,15 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
     __shared__ int32_t s_lo[kDdChunk], s_hi[kDdChunk];
     __shared__ uint32_t s_bad;                   // bit d: trial d0 + d has a bad delay
     const int tid = threadIdx.x;
-    const int64_t t0 = (int64_t)blockIdx.x * kDdSpan;
+    // block b: DM block b % n_dmb of time tile b / n_dmb, so the DM blocks of
+    // one time tile run side by side and read its channel windows from L2
+    const int64_t n_dmb = (n_dm + kDdDms - 1) / kDdDms;
+    const int64_t b = blockIdx.x;
+    const int64_t t0 = (b / n_dmb) * kDdSpan;
     const int64_t max_delay = n_samp - n_out;
     const bool has_sc = scale != nullptr;
-    for (int64_t d0 = (int64_t)blockIdx.y * kDdDms; d0 < n_dm; d0 += (int64_t)gridDim.y * kDdDms) {
+    {
+        const int64_t d0 = (b % n_dmb) * kDdDms;
         const int nd = (int)min((int64_t)kDdDms, n_dm - d0);
         float acc[kDdDms][kDdPer];
 #pragma unroll
@@ -216,8 +221,7 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
         }
         __syncthreads();
         const uint32_t bad = s_bad;
-        __syncthreads();   // read by all before the next DM block resets it
-        if (bad && status && tid == 0 && blockIdx.x == 0)
+        if (bad && status && tid == 0)
             atomicExch(&status->status, (int)SPD_ERR_INVALID_ARG);
 #pragma unroll
         for (int d = 0; d < kDdDms; ++d) {
@@ -253,10 +257,10 @@ extern "C" spd_status spd_dedisperse(const spd_plane *fb, const int32_t *delays,
         return SPD_ERR_INVALID_ARG;
     if (fb->row_offset && !fb->row_scale) return SPD_ERR_INVALID_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t gx = (n_out + kDdSpan - 1) / kDdSpan;
-    if (gx > INT32_MAX) return SPD_ERR_INVALID_ARG;
-    const int64_t gy = (n_dm + kDdDms - 1) / kDdDms;
-    const dim3 grid((unsigned)gx, (unsigned)(gy < 65535 ? gy : 65535));
+    const int64_t n_tt = (n_out + kDdSpan - 1) / kDdSpan;
+    const int64_t n_dmb = (n_dm + kDdDms - 1) / kDdDms;
+    if (n_tt > INT32_MAX / n_dmb) return SPD_ERR_INVALID_ARG;
+    const dim3 grid((unsigned)(n_tt * n_dmb));
     switch (fb->dtype) {
         case SPD_F32:
             dedisperse_kernel<SPD_F32><<<grid, kDdThreads, 0, st>>>(
