@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
     int out_dt, int64_t n_out, int64_t out_stride, spd_result *status) {
     using T = typename Elem<DT>::T;
     __shared__ __align__(16) float s_x[kDdRing][kDdWin];
-    __shared__ int32_t s_dl[kDdChunk][kDdDms];
+    __shared__ __align__(16) int32_t s_dl[kDdChunk][kDdDms];
     __shared__ int32_t s_lo[kDdChunk], s_hi[kDdChunk];
     __shared__ uint32_t s_bad;                   // bit d: trial d0 + d has a bad delay
     const int tid = threadIdx.x;
@@ -86,11 +86,12 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
     {
         const int64_t d0 = (b % n_dmb) * kDdDms;
         const int nd = (int)min((int64_t)kDdDms, n_dm - d0);
-        float acc[kDdDms][kDdPer];
+        // the thread's two outputs t0 + tid and t0 + tid + 256 of trial d as
+        // one packed pair (two IEEE adds per packed add)
+        static_assert(kDdPer == 2, "outputs per thread are one float2");
+        float2 acc[kDdDms];
 #pragma unroll
-        for (int d = 0; d < kDdDms; ++d)
-#pragma unroll
-            for (int j = 0; j < kDdPer; ++j) acc[d][j] = 0.f;
+        for (int d = 0; d < kDdDms; ++d) acc[d] = make_float2(0.f, 0.f);
         if (tid == 0) s_bad = 0u;
         for (int64_t c0 = 0; c0 < n_chan; c0 += kDdChunk) {
             const int nc = (int)min((int64_t)kDdChunk, n_chan - c0);
@@ -130,13 +131,18 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
             auto sum_channel = [&](int c, const float *w) {
                 const int lo = s_lo[c];
                 if (s_hi[c] - lo <= kDdSpread) {
+                    const int4 *dv = reinterpret_cast<const int4 *>(s_dl[c]);
 #pragma unroll
-                    for (int d = 0; d < kDdDms; ++d) {
-                        if (d < nd) {
-                            const int dl = s_dl[c][d] - lo;
+                    for (int q = 0; q < kDdDms / 4; ++q) {
+                        const int4 d4 = dv[q];   // four trials' delays, one broadcast load
+                        const int dls[4] = {d4.x - lo, d4.y - lo, d4.z - lo, d4.w - lo};
 #pragma unroll
-                            for (int j = 0; j < kDdPer; ++j)
-                                acc[d][j] = __fadd_rn(acc[d][j], w[tid + j * kDdThreads + dl]);
+                        for (int e = 0; e < 4; ++e) {
+                            if (4 * q + e < nd) {
+                                const float *p = w + tid + dls[e];
+                                acc[4 * q + e] =
+                                    __fadd2_rn(acc[4 * q + e], make_float2(p[0], p[kDdThreads]));
+                            }
                         }
                     }
                 } else {   // a wide spread: this channel straight from global memory
@@ -147,13 +153,12 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                     for (int d = 0; d < kDdDms; ++d) {
                         if (d >= nd) break;
                         const int64_t dl = s_dl[c][d];
-#pragma unroll
-                        for (int j = 0; j < kDdPer; ++j) {
-                            const int64_t t = t0 + tid + j * kDdThreads;
-                            if (t < n_out)
-                                acc[d][j] = __fadd_rn(acc[d][j],
-                                                      fb_value<DT>(row + t + dl, has_sc, sc, of));
-                        }
+                        const int64_t t = t0 + tid;
+                        if (t < n_out)
+                            acc[d].x = __fadd_rn(acc[d].x, fb_value<DT>(row + t + dl, has_sc, sc, of));
+                        if (t + kDdThreads < n_out)
+                            acc[d].y = __fadd_rn(acc[d].y,
+                                                 fb_value<DT>(row + t + kDdThreads + dl, has_sc, sc, of));
                     }
                 }
             };
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                 const int64_t t = t0 + tid + j * kDdThreads;
                 if (t < n_out)
                     store_out(out, out_dt, (d0 + d) * out_stride + t,
-                              ((bad >> d) & 1u) ? nan : acc[d][j]);
+                              ((bad >> d) & 1u) ? nan : (j ? acc[d].y : acc[d].x));
             }
         }
     }

@@ -80,3 +80,41 @@ def test_search_host_overflow_keeps_the_count(spd):
     full = spd.candidates_to_numpy(o2, count)
     keys = set(zip(full["dm"].tolist(), full["sample"].tolist()))
     assert all((int(d), int(s)) in keys for d, s in zip(recs["dm"], recs["sample"]))
+
+
+def test_search_host_from_two_threads(spd):
+    """Two host threads, each with its own stream, workspace and output,
+    search two planes at once (the copy stream of each call belongs to its
+    thread): every call gives the records of its plane alone."""
+    import threading
+    planes = [synth.ska_like(300, 20000, n_pulses=6, device=DEV, seed=80 + k).data.cpu().pin_memory()
+              for k in range(2)]
+    widths = list(range(1, 17)) + list(range(24, 129, 8))
+    cap = 300 * 20000 // 2
+
+    def run(xh, stream):
+        ws = torch.empty(spd.search_host_workspace_bytes(xh, widths, 7.0, cap), dtype=torch.uint8,
+                         device=DEV)
+        out = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
+        got = []
+        for _ in range(3):
+            c, st = spd.search_host(xh, widths, 7.0, out, workspace=ws, stream=stream)
+            got.append((c, st, _sorted(out[:c].numpy().view(spd.CAND_DTYPE).reshape(-1)).copy()))
+        return got
+
+    want = [run(xh, None)[0] for xh in planes]
+    results = [None, None]
+
+    def worker(k):
+        torch.cuda.set_device(0)
+        results[k] = run(planes[k], torch.cuda.Stream(device=DEV))
+
+    th = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for k in range(2):
+        assert results[k] is not None
+        for c, st, recs in results[k]:
+            assert (c, st) == want[k][:2] and np.array_equal(recs, want[k][2])
