@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=512)
+    ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--workload", choices=["ska", "plain", "precision", "batched", "serving",
                                            "decimated", "cluster", "plane", "dedisperse"],
