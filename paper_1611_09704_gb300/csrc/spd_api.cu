@@ -1246,11 +1246,28 @@ constexpr int kHostBlocks = 16;   // most row blocks of one call
 
 // Per host thread: the copy-out stream and the events of the row blocks (on
 // the device current when they were made), and page-locked result words.
+// Released when the thread exits (errors ignored: at process exit the
+// runtime may already be gone), and the stream and events when the thread
+// moves to another device.
 struct HostAux {
     int dev = -1;
     cudaStream_t cs = nullptr;
     cudaEvent_t ev[kHostBlocks] = {};
     spd_result *pin = nullptr;
+
+    void release_device_objects() {
+        for (int b = 0; b < kHostBlocks; ++b) {
+            if (ev[b]) (void)cudaEventDestroy(ev[b]);
+            ev[b] = nullptr;
+        }
+        if (cs) (void)cudaStreamDestroy(cs);
+        cs = nullptr;
+        dev = -1;
+    }
+    ~HostAux() {
+        release_device_objects();
+        if (pin) (void)cudaFreeHost(pin);
+    }
 };
 thread_local HostAux g_aux;
 
@@ -1265,6 +1282,7 @@ cudaError_t host_aux(HostAux **out) {
         if (e != cudaSuccess) return e;
     }
     if (a.dev != dev) {
+        a.release_device_objects();
         e = cudaStreamCreateWithFlags(&a.cs, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
         for (int b = 0; b < kHostBlocks; ++b) {

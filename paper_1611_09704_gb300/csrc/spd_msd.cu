@@ -452,14 +452,14 @@ __device__ __forceinline__ float block_sum(const float *s_y, int b) {
 // B_Nmax(i) = x[i] + ... + x[i+Nmax-1] over full windows.  Each CTA walks up
 // to kNmaxTilesPerCta consecutive tiles of one row; per tile it stages the
 // centred samples plus an (Nmax - 1)-sample halo, with 16-sample block sums.
-// A thread owns 64 consecutive starts: B at the first from the whole blocks
-// of its window (four interleaved sums) plus the partial block, then sliding
-// one sample at a time.  Per 16 starts, the even and the odd eight (one per
-// f32x2 lane) give (n, T, S) directly (sum, then squared deviations from
-// their mean), and Eq. 2 folds each into the lane's running (n, T, S); starts
-// near the row end take Eq. 1 one at a time.  At the end
-// Eq. 2 merges the lanes, then lanes of the warp and warps, into the CTA's
-// one partial.  The sd does not depend on the centring.
+// A thread owns 64 consecutive starts: B0 = B at the first, from the whole
+// blocks of its window (four interleaved sums) plus the partial block; then
+// d = B - B0 slides one sample at a time, and the thread sums d and d^2 over
+// its starts with full windows (even and odd starts in the two f32x2 lanes).
+// Its run's (n, T, S) -- n, n B0 + sum d, sum d^2 - (sum d)^2 / n -- goes
+// into the thread's running (n, T, S) by Eq. 2 once per tile.  At the end
+// Eq. 2 merges the lanes of the warp and the warps into the CTA's one
+// partial.  The sd does not depend on the centring.
 template <int DT>
 __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const NmaxArgs a) {
     using T = typename Elem<DT>::T;
@@ -487,8 +487,7 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
     const int nmax = a.nmax;
     const int b0 = tid * (kNmaxPer / 16);          // the thread's first block (tile-local)
     const int qe = 16 * b0 + nmax;                 // end of its first window
-    Acc2 acc2;      // full 16-start units
-    Acc tail_acc;   // starts near the row end
+    Acc run_acc;    // the thread's runs: one Eq. 2 merge per tile
     for (int64_t tl = tl0; tl < tl1; ++tl) {
         const int64_t t0 = tl * (int64_t)kNmaxTile;
         __syncthreads();   // the previous tile's reads of s_y / s_bs are done
@@ -560,7 +559,16 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
         for (; b < be; ++b) w0 += s_bs[b];
         float tail = 0.f;
         for (int q = (qe & ~15); q < qe; ++q) tail += s_y[npad(q)];
-        float B = ((w0 + w1) + (w2 + w3)) + tail;
+        const float B0 = ((w0 + w1) + (w2 + w3)) + tail;
+        // B slides as its difference d = B - B0 from the thread's first start:
+        // over its full-window starts the thread keeps sums of d and d^2 (even
+        // and odd starts in the two packed lanes), so that (n, T, S) of its run
+        // is n, n B0 + sum d and sum d^2 - (sum d)^2 / n, merged once per
+        // tile.  d stays near 0 within a run of 64 starts, so the difference
+        // of sums loses little.
+        float Bd = 0.f;
+        float2 Td = f2(0.f), Sd = f2(0.f);
+        int nrun = 0;
         // starts t0 + 16 b0 + k are full windows while k < nvalid
         const int64_t nvalid = a.n_samp - nmax - (t0 + 16 * b0) + 1;
 #pragma unroll 1
@@ -587,32 +595,46 @@ __global__ void __launch_bounds__(kNmaxThreads, 5) nmax_partial_kernel(const Nma
                     hi[k] = s_y[npad(q)];
                 }
             }
-            // B slides by hi - lo per start (the differences as f32x2 pairs)
-            float2 bw[8];   // bw[k] = (B at unit start + 2k, B at unit start + 2k + 1)
+            // d slides by hi - lo per start (the differences as f32x2 pairs)
+            float2 bw[8];   // bw[k] = (d at unit start + 2k, d at unit start + 2k + 1)
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const float2 dl = __ffma2_rn(make_float2(lo[2 * k], lo[2 * k + 1]), f2(-1.f),
                                              make_float2(hi[2 * k], hi[2 * k + 1]));
-                bw[k].x = B;
-                B += dl.x;
-                bw[k].y = B;
-                B += dl.y;
+                bw[k].x = Bd;
+                Bd += dl.x;
+                bw[k].y = Bd;
+                Bd += dl.y;
             }
             const int64_t nv = nvalid - 16 * c;
             if (nv >= 16) {
-                // (T, S) of the even and of the odd eight, Eq. 2 into the lanes
-                float2 U, S8;
-                Acc2::direct_8(bw, U, S8);
-                acc2.fold8(U, S8);
-            } else {
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (k < nv) tail_acc.add1(k & 1 ? bw[k >> 1].y : bw[k >> 1].x);
+                for (int k = 0; k < 8; ++k) {
+                    Td = __fadd2_rn(Td, bw[k]);
+                    Sd = __ffma2_rn(bw[k], bw[k], Sd);
+                }
+                nrun += 16;
+            } else if (nv > 0) {   // near the row end: the starts with full windows
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float2 dm = make_float2(2 * k < nv ? bw[k].x : 0.f,
+                                                  2 * k + 1 < nv ? bw[k].y : 0.f);
+                    Td = __fadd2_rn(Td, dm);
+                    Sd = __ffma2_rn(dm, dm, Sd);
+                }
+                nrun += (int)nv;
             }
         }
+        if (nrun) {   // the run's (n, T, S), T with the product n B0 kept exactly
+            const float n = (float)nrun;
+            const float td = Td.x + Td.y;
+            const float sr = fmaf(-td, td / n, Sd.x + Sd.y);
+            const float th = n * B0;
+            const float tlo = fmaf(n, B0, -th) + td;
+            run_acc.merge(n, th, tlo, fmaxf(sr, 0.f));
+        }
     }
-    Acc acc = acc2.lanes();
-    acc.merge(tail_acc.m, tail_acc.Th, tail_acc.Tl, tail_acc.S);
+    Acc acc = run_acc;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc.merge_down(off);
     __shared__ float4 s_w[kNmaxThreads / 32];
