@@ -139,3 +139,24 @@ def test_coupled_stream_matches_oracle(spd):
     found = np.concatenate([c[2] for c in calls])
     for (k, t0, w, amp) in pulses:          # each dispersed pulse found at its trial
         assert np.any((found["dm"] == k) & (np.abs(found["sample"] - t0) <= w))
+
+
+def test_full_size_sampled_trials_match_oracle(spd):
+    """The bench's workload (256 channels 1200-1500 MHz at 64 us, 256 trials
+    at DM 0..100, 2^18 output samples) in its launch configuration: every
+    output of 8 trials spread over the range against the oracle's
+    de-dispersion of those trials."""
+    n_chan, n_dm, n_out = 256, 256, 1 << 18
+    dms = np.linspace(0.0, 100.0, n_dm)
+    delays_np = synth.dispersion_delays(n_chan, dms)
+    fb = synth.filterbank(n_chan, n_out + int(delays_np.max()), dms=dms,
+                          pulses=((100, 5000, 8, 0.5),), device=DEV, seed=1611_8)
+    assert fb.n_out == n_out
+    out = spd.dedisperse(fb.data, torch.from_numpy(fb.delays).to(DEV), n_out)
+    sel = np.arange(0, n_dm, 37)
+    got = out[torch.from_numpy(sel).to(DEV)].cpu().numpy().astype(np.float64)
+    x = synth.to_host_numpy(fb.data)
+    want = oracle.dedisperse(x, np.ascontiguousarray(fb.delays[sel]), n_out)
+    mag = oracle.dedisperse(np.abs(x).astype(np.float32), np.ascontiguousarray(fb.delays[sel]),
+                            n_out)
+    assert np.all(np.abs(got - want) <= 2e-7 * n_chan * mag + 1e-30), np.abs(got - want).max()
