@@ -33,6 +33,7 @@ def _sorted(r):
 @pytest.mark.parametrize("dtype,n_dm,n_samp,scope", [
     ("f32", 600, 20001, 0),     # two row blocks of 300, ragged length
     ("f16", 300, 12000, 1),     # one block, per-row MSD, host per-row scale
+    ("bf16", 520, 9000, 1),     # two blocks, per-row MSD: each block's tables offset by its rows
 ])
 def test_search_host_matches_oracle_and_device(spd, dtype, n_dm, n_samp, scope):
     sp = synth.ska_like(n_dm, n_samp, n_pulses=8, device=DEV, seed=71)
