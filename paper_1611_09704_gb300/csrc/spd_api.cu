@@ -173,23 +173,9 @@ int prog_kmax(const RangeProg &prog) {
     return k;
 }
 
-// Blocks of 16 positions staged per tile: the tile, the halo and slack for
-// window loads that run past the last width.
-int prog_R(const RangeProg &prog) { return (kTile + prog.wmax + 32 + 15) / 16 + 1; }
-int prog_span(const RangeProg &prog) { return kTile + prog.wmax - 1; }
+// Bytes of the raw staging buffer for a window of `span` positions (whole
+// 16-byte pieces).
 int raw_bytes_of(int span, int dtype) { return (int)((span * elem_bytes(dtype) + 15) / 16 * 16); }
-
-// Shared memory of one detect CTA: two raw staging buffers, the centred
-// samples and window sums (20 words per 16 positions), per-block sums and
-// prefix bounds, 1/sigma_w and the width per eval index, 1/sigma_w per group.
-size_t launch_smem(int R, int raw_bytes, int max_eval, int G) {
-    size_t b = 16 + 2 * (size_t)raw_bytes;
-    b += (size_t)(G ? 2 : 1) * 20 * R * sizeof(float);
-    b += (size_t)R * (3 + 5) * sizeof(float);   // block sums, max/min prefix, max table
-    b += (size_t)max_eval * sizeof(float) + 16 + kMaxCodeGroups * 16;
-    b += (size_t)max_eval * sizeof(uint16_t);
-    return (b + 15) / 16 * 16;
-}
 
 // --------------------------------------------------------- detect workspace
 
@@ -259,11 +245,11 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
     rd.inv_tab = c.inv_tab;
     rd.mu_tab = c.mu_tab;
     rd.flags = c.flags;
-    rd.tiles_per_row = (p->n_samp + kTile - 1) / kTile;
+    rd.tiles_per_row = 0;   // the tile geometry is set by run_launch
     rd.vec_ok = plane_vec_ok(p);
     rd.per_row = scope == SPD_MSD_PER_ROW;
-    rd.R = prog_R(prog);
-    rd.span = prog_span(prog);
+    rd.R = 0;
+    rd.span = 0;
     rd.n_emit = p->n_samp;
     rd.sample_base = 0;
     rd.sample_shift = 0;
@@ -276,15 +262,16 @@ spd_status range_consts(const spd_plane *p, const RangeProg &prog, const spd_msd
 thread_local uint64_t g_wait_ns = 2000000000ull;
 thread_local uint32_t g_extra_tx = 0;
 
-// One detect launch over ranges rd[0 .. n) (same storage type and G).
-// The candidate search takes tiles of 16 * threads starts (threads 128 or
-// 256; 0 = the default); the plane output tiles of kTile.
+// One search-kernel launch over ranges rd[0 .. n) (same storage type and G):
+// candidates, or with snr_out the plane output (every group evaluated).
+// Tiles of 16 starts per unit, units = the threads (128 or 256, 0 = the
+// default; plane output 256) less the halo's blocks.
 spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out, int64_t cap,
                       spd_result *result, float *snr_out, uint16_t *width_out,
                       int64_t out_stride, int ctas_per_sm, cudaStream_t st, int threads = 0) {
     static thread_local Launch L;
     memset(&L, 0, sizeof(L));
-    const int nt = (threads == 128 || threads == 256) ? threads : kSearchThreads;
+    const int nt = !snr_out && (threads == 128 || threads == 256) ? threads : kSearchThreads;
     // candidate search: U units of 16 starts per tile, the threads less the
     // widest range's halo blocks when that leaves one block per thread
     int halo = 0;
@@ -297,17 +284,15 @@ spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out,
     int R = 0, raw = 0, max_eval = 0, G = rd[0].prog.G;
     for (int i = 0; i < n; ++i) {
         L.rng[i] = rd[i];
-        if (!snr_out) {
-            const int tile = kX * units;
-            L.rng[i].tiles_per_row = (rd[i].n_samp + tile - 1) / tile;
-            L.rng[i].R = (tile + rd[i].prog.wmax + 32 + 15) / 16 + 1;
-            // the window rounded up to whole 16-byte pieces: one bulk copy
-            // brings all of it (a tail fetched by plain loads would put a
-            // global-memory latency into every tile's staging); the extra
-            // samples lie in no evaluated window
-            const int per16 = 16 / (int)elem_bytes(dtype);
-            L.rng[i].span = (tile + rd[i].prog.wmax - 1 + per16 - 1) / per16 * per16;
-        }
+        const int tile = kX * units;
+        L.rng[i].tiles_per_row = (rd[i].n_samp + tile - 1) / tile;
+        L.rng[i].R = (tile + rd[i].prog.wmax + 32 + 15) / 16 + 1;
+        // the window rounded up to whole 16-byte pieces: one bulk copy brings
+        // all of it (a tail fetched by plain loads would put a global-memory
+        // latency into every tile's staging); the extra samples lie in no
+        // evaluated window
+        const int per16 = 16 / (int)elem_bytes(dtype);
+        L.rng[i].span = (tile + rd[i].prog.wmax - 1 + per16 - 1) / per16 * per16;
         L.rng[i].tile0 = tiles;
         tiles += L.rng[i].n_dm * L.rng[i].tiles_per_row;
         R = L.rng[i].R > R ? L.rng[i].R : R;
@@ -328,14 +313,10 @@ spd_status run_launch(const RangeDesc *rd, int n, int dtype, spd_candidate *out,
     L.out_stride = out_stride;
     L.wait_ns = g_wait_ns;
     L.extra_tx = g_extra_tx;
-    if (snr_out) {   // plane output: every sample's best SNR and width
-        const size_t smem = launch_smem(R, raw, max_eval, G);
-        if (smem > 227 * 1024) return SPD_ERR_UNSUPPORTED;
-        SPD_CK(launch_detect(L, dtype, G, true, max_eval > 64, smem, ctas_per_sm, st));
-        return SPD_OK;
-    }
+    // plane output (every sample's best SNR and width) evaluates every group
+    // and needs no bound tables
     int kmax = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && !snr_out; ++i) {
         const int k = prog_kmax(rd[i].prog);
         kmax = k > kmax ? k : kmax;
     }

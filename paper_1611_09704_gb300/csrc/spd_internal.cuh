@@ -69,8 +69,6 @@ struct NmaxArgs {
 // ------------------------------------------------------------------ detect
 
 constexpr int kX = 16;              // consecutive samples owned by one thread
-constexpr int kThreads = 256;       // threads per CTA
-constexpr int kTile = kX * kThreads; // samples of one row searched per CTA
 
 // One group of evaluated widths (host-compiled from the width list).  The
 // running boxcar sum B of every start sample i starts as
@@ -252,8 +250,6 @@ cudaError_t launch_merge_shards(const MsdPart *parts, int n, int what, int nmax,
                                 spd_msd_stats *out, cudaStream_t s);
 cudaError_t launch_nmax(const NmaxArgs &a, int dtype, MsdPart *scratch, int n_scratch,
                         spd_msd_stats *out, cudaStream_t s);
-cudaError_t launch_detect(const Launch &L, int dtype, int G, bool plane_out, bool multi_block,
-                          size_t smem, int ctas_per_sm, cudaStream_t s);
 // The candidate search (search kernel): same launch description with the
 // ranges' tiles of 16 * threads starts (threads = 128 or 256), kmax set.
 cudaError_t launch_search(const Launch &L, int dtype, int G, bool multi_block, size_t smem,

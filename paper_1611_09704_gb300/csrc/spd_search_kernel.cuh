@@ -389,7 +389,7 @@ struct TilePos {
     int64_t row, col;
 };
 
-template <int DT, int G, bool MG, int NT>
+template <int DT, int G, bool MG, int NT, bool PL>
 __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_constant__ Launch L) {
     constexpr int kThreads = NT;
     // units of 16 starts per tile: NT less the halo blocks when the whole
@@ -432,27 +432,33 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
     // width lists, dense candidates) take fewer of them.  The chunks in
     // flight at one time are neighbours, so a window's halo is still in L2.
     // The counter (the result word's reserved field) is 0 at launch; the CTA
-    // that gets the last claim of all sets it back to 0.
+    // that gets the last claim of all sets it back to 0.  Plane output (PL),
+    // where every tile costs the same, takes one fixed run of tiles per CTA
+    // instead, without a counter.
     auto counter = [&]() { return reinterpret_cast<unsigned *>(&L.result->reserved0); };
-    int64_t tile = (int64_t)blockIdx.x * L.chunk;   // the host launches at most n_chunks CTAs
-    // the launch's tile count and chunk length, read from shared memory where
-    // needed (kept out of registers through the search)
+    // the host launches at most n_chunks CTAs (PL: at most n_tiles)
+    int64_t tile = PL ? (int64_t)blockIdx.x * L.n_tiles / gridDim.x
+                      : (int64_t)blockIdx.x * L.chunk;
+    // the launch's tile count (PL: the end of the CTA's run) and chunk length,
+    // read from shared memory where needed (kept out of registers through the
+    // search)
     __shared__ long long s_ntiles;
     __shared__ int s_chunk;
     if (tid == 0) {
-        s_ntiles = L.n_tiles;
+        s_ntiles = PL ? (int64_t)(blockIdx.x + 1) * L.n_tiles / gridDim.x : L.n_tiles;
         s_chunk = L.chunk;
     }
     __syncthreads();
     // chunks are aligned and a power of two long: a tile is its chunk's last
     // when the next one starts a chunk
     auto chunk_ends = [&]() {
+        if (PL) return tile + 1 >= s_ntiles;
         return (((uint32_t)tile + 1u) & (uint32_t)(s_chunk - 1)) == 0u || tile + 1 == s_ntiles;
     };
     __shared__ long long s_next;                // first tile of the next chunk, or -1
     __shared__ unsigned s_claim;                // thread 0's claim for the chunk after this one
     unsigned claim = 0;                         // thread 0, until it parks it in s_claim
-    bool claimed = tid == 0;
+    bool claimed = !PL && tid == 0;
     if (claimed) claim = atomicAdd(counter(), 1u);
 
     const bool tma = L.rng[0].vec_ok != 0;   // all ranges of a launch agree (the host checks)
@@ -505,12 +511,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         if (!chunk_ends()) {
             nt = tile + 1;
         } else {
-            const unsigned v = s_claim;
-            const int64_t ch = s_chunk;
-            const int64_t n_chunks = (s_ntiles + ch - 1) / ch;
-            const int64_t nc = (int64_t)gridDim.x + (int64_t)v;
-            if (nc < n_chunks) nt = nc * ch;
-            else if ((int64_t)v == n_chunks - 1) atomicExch(counter(), 0u);   // the last claim
+            if (!PL) {
+                const unsigned v = s_claim;
+                const int64_t ch = s_chunk;
+                const int64_t n_chunks = (s_ntiles + ch - 1) / ch;
+                const int64_t nc = (int64_t)gridDim.x + (int64_t)v;
+                if (nc < n_chunks) nt = nc * ch;
+                else if ((int64_t)v == n_chunks - 1) atomicExch(counter(), 0u);   // the last claim
+            }
             s_next = nt;
         }
         if (tma && nt >= 0) issue(nt == tile + 1 ? advance(pos) : pos_of(nt));
@@ -585,7 +593,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
                 if (nt < 0) break;
                 tile = nt;
                 pos = pos_of(tile);
-                claimed = tid == 0;
+                claimed = !PL && tid == 0;
                 if (claimed) claim = atomicAdd(counter(), 1u);
             }
         }
@@ -611,7 +619,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         } else {
             __syncthreads();
         }
-        bool held = k && tid == kAtomicThread;   // a reservation not yet published
+        bool held = !PL && k && tid == kAtomicThread;   // a reservation not yet published
         unsigned long long rbase = 0;
         if (held) rbase = reserve();
         {
@@ -639,6 +647,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
             claimed = false;
             if (tid == 0) issue_next();
             flush();
+            if (PL && tid < U) {   // no SNR: NaN, width 0
+                const int64_t i0 = t0 + (int64_t)tid * kX;
+#pragma unroll
+                for (int q = 0; q < kX; ++q) {
+                    if (i0 + q < rd.n_samp) {
+                        L.snr_out[row * L.out_stride + i0 + q] = __int_as_float(0x7fc00000);
+                        L.width_out[row * L.out_stride + i0 + q] = 0;
+                    }
+                }
+            }
             __syncthreads();   // every warp has read its slice before the counts change
             if (lane == 0) s_wsum[warp] = 0;
             continue;
@@ -746,66 +764,68 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         if (tid == 0) issue_next();
         flush();           // the last tile's records, into the slice reserved above
 
-        // ---- prefix values at block starts, their maxima, energy prefix
-        {
-            // prefix of the chunk totals, by a warp scan (at most 32 chunks)
-            const int nch = (R + 31) >> 5;
-            float ws = lane < nch ? s_wt[lane] : 0.f, wq = lane < nch ? s_wq[lane] : 0.f;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float us = __shfl_up_sync(0xffffffffu, ws, o);
-                const float uq = __shfl_up_sync(0xffffffffu, wq, o);
-                if (lane >= o) {
-                    ws += us;
-                    wq += uq;
-                }
-            }
-            const int kl = KM < 3 ? KM : 3;
-            float mag = 0.f;
-            for (int r = 0; r * kThreads < R; ++r) {
-                const int c = r * kThreads + tid;
-                if (r * kThreads + warp * 32 >= R) break;   // warp-uniform
-                const int chunk = c >> 5;   // the same for the whole warp
-                // exclusive prefix of chunk `chunk` and of the next one
-                const float pre = __shfl_sync(0xffffffffu, ws, (chunk - 1) & 31);
-                const float pre_n = __shfl_sync(0xffffffffu, ws, chunk & 31);
-                const float preq = __shfl_sync(0xffffffffu, wq, (chunk - 1) & 31);
-                const float preq_n = __shfl_sync(0xffffffffu, wq, chunk & 31);
-                if (c >= R) continue;
-                const float P = (chunk ? pre : 0.f) + s_ex[c];
-                const float mx = P + s_rh[c];
-                const float mn = P + s_rl[c];
-                s_mx[c] = mx;
-                s_mn[c] = mn;
-                if (fabsf(mx) < INFINITY) mag = fmaxf(mag, fabsf(mx));
-                if (fabsf(mn) < INFINITY) mag = fmaxf(mag, fabsf(mn));
-                s_pq[c] = (chunk ? preq : 0.f) + s_eq[c];
-                if (c == R - 1) s_pq[R] = preq_n;
-                if (kl > 0) {
-                    float m = mx;
-#pragma unroll
-                    for (int j = 1; j < 8; ++j) {
-                        if (j >= (1 << kl)) break;
-                        const int b = min(c + j, R - 1);
-                        const float Pb = ((b >> 5) == chunk ? (chunk ? pre : 0.f) : pre_n) + s_ex[b];
-                        m = fmaxf(m, Pb + s_rh[b]);
-                        if (j == 1) s_mx[RM + c] = m;
-                        if (j == 3) s_mx[2 * RM + c] = m;
-                        if (j == 7) s_mx[3 * RM + c] = m;
+        if (!PL) {   // the bounds' data (plane output evaluates every group)
+            // ---- prefix values at block starts, their maxima, energy prefix
+            {
+                // prefix of the chunk totals, by a warp scan (at most 32 chunks)
+                const int nch = (R + 31) >> 5;
+                float ws = lane < nch ? s_wt[lane] : 0.f, wq = lane < nch ? s_wq[lane] : 0.f;
+    #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float us = __shfl_up_sync(0xffffffffu, ws, o);
+                    const float uq = __shfl_up_sync(0xffffffffu, wq, o);
+                    if (lane >= o) {
+                        ws += us;
+                        wq += uq;
                     }
                 }
+                const int kl = KM < 3 ? KM : 3;
+                float mag = 0.f;
+                for (int r = 0; r * kThreads < R; ++r) {
+                    const int c = r * kThreads + tid;
+                    if (r * kThreads + warp * 32 >= R) break;   // warp-uniform
+                    const int chunk = c >> 5;   // the same for the whole warp
+                    // exclusive prefix of chunk `chunk` and of the next one
+                    const float pre = __shfl_sync(0xffffffffu, ws, (chunk - 1) & 31);
+                    const float pre_n = __shfl_sync(0xffffffffu, ws, chunk & 31);
+                    const float preq = __shfl_sync(0xffffffffu, wq, (chunk - 1) & 31);
+                    const float preq_n = __shfl_sync(0xffffffffu, wq, chunk & 31);
+                    if (c >= R) continue;
+                    const float P = (chunk ? pre : 0.f) + s_ex[c];
+                    const float mx = P + s_rh[c];
+                    const float mn = P + s_rl[c];
+                    s_mx[c] = mx;
+                    s_mn[c] = mn;
+                    if (fabsf(mx) < INFINITY) mag = fmaxf(mag, fabsf(mx));
+                    if (fabsf(mn) < INFINITY) mag = fmaxf(mag, fabsf(mn));
+                    s_pq[c] = (chunk ? preq : 0.f) + s_eq[c];
+                    if (c == R - 1) s_pq[R] = preq_n;
+                    if (kl > 0) {
+                        float m = mx;
+    #pragma unroll
+                        for (int j = 1; j < 8; ++j) {
+                            if (j >= (1 << kl)) break;
+                            const int b = min(c + j, R - 1);
+                            const float Pb = ((b >> 5) == chunk ? (chunk ? pre : 0.f) : pre_n) + s_ex[b];
+                            m = fmaxf(m, Pb + s_rh[b]);
+                            if (j == 1) s_mx[RM + c] = m;
+                            if (j == 3) s_mx[2 * RM + c] = m;
+                            if (j == 7) s_mx[3 * RM + c] = m;
+                        }
+                    }
+                }
+    #pragma unroll
+                for (int o = 16; o; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+                if (lane == 0) atomicMax(&s_mag, __float_as_int(mag));
             }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(0xffffffffu, mag, o));
-            if (lane == 0) atomicMax(&s_mag, __float_as_int(mag));
-        }
-        __syncthreads();   // (C)
-        for (int lv = 4; lv <= KM; ++lv) {
-            const float *lo = s_mx + (lv - 1) * RM;
-            const int h = 1 << (lv - 1);
-            for (int c = tid; c < R; c += kThreads)
-                s_mx[lv * RM + c] = fmaxf(lo[c], lo[min(c + h, R - 1)]);
-            __syncthreads();
+            __syncthreads();   // (C)
+            for (int lv = 4; lv <= KM; ++lv) {
+                const float *lo = s_mx + (lv - 1) * RM;
+                const int h = 1 << (lv - 1);
+                for (int c = tid; c < R; c += kThreads)
+                    s_mx[lv * RM + c] = fmaxf(lo[c], lo[min(c + h, R - 1)]);
+                __syncthreads();
+            }
         }
 
         // ---- search of the unit's 16 starts (widest group first)
@@ -852,23 +872,27 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         for (int gi = tid < U ? rp.n_groups - 1 : -1; gi >= 0; --gi) {
             const int4 ga = s_gr[2 * gi];
             const int4 gb = s_gr[2 * gi + 1];
-            float rmax;
-            if (gb.y >= 0) {
-                rmax = fmaxf(s_mx[tid + ga.z], s_mx[tid + ga.w]);
-            } else {
-                rmax = -INFINITY;
-                for (int jb = tid + ga.z; jb <= tid + ga.w; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
+            if (!PL) {
+                float rmax;
+                if (gb.y >= 0) {
+                    rmax = fmaxf(s_mx[tid + ga.z], s_mx[tid + ga.w]);
+                } else {
+                    rmax = -INFINITY;
+                    for (int jb = tid + ga.z; jb <= tid + ga.w; ++jb) rmax = fmaxf(rmax, s_mx[jb]);
+                }
+                // prefix bound, with the margin for the rounding of the FP32
+                // prefix; a non-positive bound caps every SNR at 0; NaN stays NaN
+                const float pbound = fmaxf(rmax + cslack, 0.f) * __int_as_float(gb.z);
+                // energy bound (squared); the prefix of energies is non-negative
+                // and rounds by a few ulp of its larger end.  The factor covers
+                // this group and all narrower ones, whose windows lie in the
+                // same blocks
+                const float ebound2 =
+                    fmaf(s_pq[tid + gb.x], 1.000008f, -pq0) * __int_as_float(gb.w);
+                if (ebound2 < lim2) break;
+                // NaN bounds (windows past the row end) never prune
+                if (pbound < lim_lo) continue;
             }
-            // prefix bound, with the margin for the rounding of the FP32 prefix;
-            // a non-positive bound caps every SNR at 0; NaN stays NaN
-            const float pbound = fmaxf(rmax + cslack, 0.f) * __int_as_float(gb.z);
-            // energy bound (squared); the prefix of energies is non-negative and
-            // rounds by a few ulp of its larger end.  The factor covers this
-            // group and all narrower ones, whose windows lie in the same blocks
-            const float ebound2 = fmaf(s_pq[tid + gb.x], 1.000008f, -pq0) * __int_as_float(gb.w);
-            if (ebound2 < lim2) break;
-            // NaN bounds (windows past the row end) never prune
-            if (pbound < lim_lo) continue;
             Group g;
             g.off = (int16_t)(ga.x & 0xffff);
             g.count = (int16_t)(ga.x >> 16);
@@ -883,7 +907,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
                     cur_blk = blk;
                 }
             }
-            if (g.flags & kGroupRefine) {
+            if (!PL && (g.flags & kGroupRefine)) {
                 float bq[kX];
 #pragma unroll
                 for (int q = 0; q < kX; ++q) bq[q] = MG ? fmaxf(cb[q], ob[q]) : cb[q];
@@ -900,8 +924,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
                 if ((g.off & 15) == 0) {
                     const int o = g.off >> 4;
                     float D;
-                    if (lastO >= o && lastO - o <= 16) {
-                        // widest group first: take off the blocks between
+                    // widest group first: take off the blocks between.  Not
+                    // from a sum that met the row end (-inf): the blocks of
+                    // this group may all lie inside the row
+                    if (lastO >= o && lastO - o <= 16 && lastD > -INFINITY) {
                         D = lastD;
                         for (int b = o; b < lastO; ++b) D = __fsub_rn(D, s_bs[tid + b]);
                     } else {
@@ -940,6 +966,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
                 eval_generic(cb, B, yb, g, 1, s_inv);
             }
             // the bar rises to the smallest best of the unit
+            if (PL) continue;
             float mb;
             if (MG) {
                 mb = fmaxf(cb[0], ob[0]);
@@ -960,6 +987,51 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
             }
         }
         if (MG && cur_blk >= 0) merge_block();
+
+        if (PL) {   // every sample's best SNR (truncated to 2^-17) and its width
+            const int64_t i0 = t0 + (int64_t)tid * kX;
+            if (tid < U && i0 < rd.n_samp) {
+                float snr[kX];
+                int wdt[kX];
+#pragma unroll
+                for (int q = 0; q < kX; ++q) {
+                    const uint32_t bits = __float_as_uint(MG ? ob[q] : cb[q]);
+                    const int eb = MG ? 64 * (int)((obk[q >> 2] >> (8 * (q & 3))) & 0xffu) : 0;
+                    const int wi = eb + 63 - (int)(bits & 63u);
+                    snr[q] = __uint_as_float(bits & 0xFFFFFFC0u);
+                    wdt[q] = wi < rp.n_eval ? (int)s_ew[wi] : 0;
+                }
+                float *so = L.snr_out + row * L.out_stride + i0;
+                uint16_t *wo = L.width_out + row * L.out_stride + i0;
+                const bool al = ((reinterpret_cast<uintptr_t>(so) | reinterpret_cast<uintptr_t>(wo)) &
+                                 15) == 0;
+                if (al && i0 + kX <= rd.n_samp) {
+#pragma unroll
+                    for (int v = 0; v < kX / 4; ++v)
+                        reinterpret_cast<float4 *>(so)[v] =
+                            make_float4(snr[4 * v], snr[4 * v + 1], snr[4 * v + 2], snr[4 * v + 3]);
+#pragma unroll
+                    for (int v = 0; v < kX / 8; ++v) {
+                        uint4 u;
+                        u.x = (uint32_t)wdt[8 * v] | ((uint32_t)wdt[8 * v + 1] << 16);
+                        u.y = (uint32_t)wdt[8 * v + 2] | ((uint32_t)wdt[8 * v + 3] << 16);
+                        u.z = (uint32_t)wdt[8 * v + 4] | ((uint32_t)wdt[8 * v + 5] << 16);
+                        u.w = (uint32_t)wdt[8 * v + 6] | ((uint32_t)wdt[8 * v + 7] << 16);
+                        reinterpret_cast<uint4 *>(wo)[v] = u;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kX; ++q) {
+                        if (i0 + q < rd.n_samp) {
+                            so[q] = snr[q];
+                            wo[q] = (uint16_t)wdt[q];
+                        }
+                    }
+                }
+            }
+            if (lane == 0) s_wsum[warp] = 0;
+            continue;
+        }
 
         // ---- threshold (Sec. 2.4, inclusive); the records wait for the next tile
         uint32_t mask = 0;
@@ -986,6 +1058,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
         pwtot = __reduce_add_sync(0xffffffffu, __popc(mask));
         if (lane == 0) s_wsum[warp] = pwtot;
     }
+    if (PL) return;
     // the last tile's records
     __syncthreads();
     if (tid == kAtomicThread) publish(reserve());
@@ -993,24 +1066,27 @@ __global__ void __launch_bounds__(NT, 512 / NT) search_kernel(const __grid_const
     flush();
 }
 
-template <int DT, int G, int NT>
+template <int DT, int G, int NT, bool PL>
 cudaError_t launch_sgn(const Launch &L, bool mg, size_t smem, int ctas_per_sm, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    void (*k)(const Launch) = mg ? search_kernel<DT, G, true, NT> : search_kernel<DT, G, false, NT>;
+    void (*k)(const Launch) =
+        mg ? search_kernel<DT, G, true, NT, PL> : search_kernel<DT, G, false, NT, PL>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
-    // chunks of 1 to 16 tiles (a power of two), about 8 per CTA at least
+    // chunks of 1 to 16 tiles (a power of two), about 8 per CTA at least;
+    // plane output: one run of tiles per CTA
     const int64_t gmax = (int64_t)sms * per_sm;
     int64_t ch = 16;
     while (ch > 1 && L.n_tiles < 8 * gmax * ch) ch >>= 1;
+    if (PL) ch = 1;
     Launch Lc = L;
     Lc.chunk = (int32_t)ch;
     const int64_t n_chunks = (L.n_tiles + ch - 1) / ch;
@@ -1023,8 +1099,9 @@ cudaError_t launch_sgn(const Launch &L, bool mg, size_t smem, int ctas_per_sm, c
 template <int DT, int G>
 cudaError_t launch_sg(const Launch &L, bool mg, size_t smem, int ctas_per_sm, int threads,
                       cudaStream_t s) {
-    return threads == 128 ? launch_sgn<DT, G, 128>(L, mg, smem, ctas_per_sm, s)
-                          : launch_sgn<DT, G, 256>(L, mg, smem, ctas_per_sm, s);
+    if (L.snr_out) return launch_sgn<DT, G, 256, true>(L, mg, smem, ctas_per_sm, s);
+    return threads == 128 ? launch_sgn<DT, G, 128, false>(L, mg, smem, ctas_per_sm, s)
+                          : launch_sgn<DT, G, 256, false>(L, mg, smem, ctas_per_sm, s);
 }
 
 }  // namespace

@@ -108,6 +108,21 @@ def test_width_programs(spd, widths):
     _full_case(spd, sp.data, sp.n_samp, widths, 7.0)
 
 
+def test_wide_pulses_at_the_row_end(spd):
+    """Top-hats whose windows end a few samples before the row end, found by
+    the coarse groups of the 46-width list: the groups' start sums must not
+    come from a wider group whose windows met the row end."""
+    n_samp = 12000
+    sp = synth.ska_like(4, n_samp, n_pulses=0, mean=0.0, sd=1.0, drift_amp=0.0, device=DEV,
+                        seed=77)
+    for r, w in enumerate((40, 100, 184, 56)):
+        synth.inject_tophat(sp.data, r, n_samp - w - 3 * r - 2, w, 15.0 / math.sqrt(w))
+    widths = list(range(1, 17)) + list(range(24, 257, 8))
+    count, best_o = _full_case(spd, sp.data, n_samp, widths, 7.0)
+    for r, w in enumerate((40, 100, 184, 56)):
+        assert best_o[r, n_samp - w - 3 * r - 2] >= 7.0
+
+
 @pytest.mark.parametrize("widths", [list(range(1, 4097)), list(range(8, 4097, 8))])
 def test_maximum_width_lists(spd, widths):
     """The API's limits: all 4096 widths (the largest group scale, 64 groups,
