@@ -121,8 +121,14 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
                     }
                 }
                 if (hi < 0) lo = hi = 0;
-                for (int d = 0; d < nd; ++d)
-                    if (s_dl[c][d] < 0) s_dl[c][d] = lo;
+                // delays relative to the channel's smallest; a bad delay and
+                // the trials past the block's last read offset 0 (their sums
+                // are never stored)
+#pragma unroll
+                for (int d = 0; d < kDdDms; ++d) {
+                    const int v = s_dl[c][d];
+                    s_dl[c][d] = (d < nd && v >= 0) ? v - lo : 0;
+                }
                 s_lo[c] = lo;
                 s_hi[c] = hi;
             }
@@ -135,14 +141,12 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
 #pragma unroll
                     for (int q = 0; q < kDdDms / 4; ++q) {
                         const int4 d4 = dv[q];   // four trials' delays, one broadcast load
-                        const int dls[4] = {d4.x - lo, d4.y - lo, d4.z - lo, d4.w - lo};
+                        const int dls[4] = {d4.x, d4.y, d4.z, d4.w};
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            if (4 * q + e < nd) {
-                                const float *p = w + tid + dls[e];
-                                acc[4 * q + e] =
-                                    __fadd2_rn(acc[4 * q + e], make_float2(p[0], p[kDdThreads]));
-                            }
+                            const float *p = w + tid + dls[e];
+                            acc[4 * q + e] =
+                                __fadd2_rn(acc[4 * q + e], make_float2(p[0], p[kDdThreads]));
                         }
                     }
                 } else {   // a wide spread: this channel straight from global memory
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kDdThreads) dedisperse_kernel(
 #pragma unroll
                     for (int d = 0; d < kDdDms; ++d) {
                         if (d >= nd) break;
-                        const int64_t dl = s_dl[c][d];
+                        const int64_t dl = (int64_t)lo + s_dl[c][d];
                         const int64_t t = t0 + tid;
                         if (t < n_out)
                             acc[d].x = __fadd_rn(acc[d].x, fb_value<DT>(row + t + dl, has_sc, sc, of));
